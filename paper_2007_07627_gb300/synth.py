@@ -1,0 +1,242 @@
+"""Seeded synthetic point-set pairs shaped like the scans of the paper's experiments.
+
+This module holds none of the registration method's arithmetic. It samples
+surfaces (torus, sum-of-Gaussian-bumps height field, union of ellipsoids),
+crops a pair to a stated overlap with two parallel half-spaces, adds Gaussian
+noise and uniform outliers the way the paper's synthetic tests do (crops,
+noise and uniform outliers: Sec. 6.1, Fig. 5), and moves the source by a
+seeded rigid motion. Both the CUDA path and the FP64 oracle consume exactly the
+float32 arrays produced here; nothing here depends on either of them.
+
+Random numbers come from numpy's Philox counter-based generator (Salmon et al.,
+SC'11), keyed by the seed, so every pair is reproducible from its seed alone.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+from scipy.spatial.transform import Rotation
+
+__all__ = [
+    "Pair", "rng", "random_rigid", "torus_pair", "height_field_pair",
+    "ellipsoid_pair", "config_pair", "CONFIG_SEEDS",
+]
+
+# Seed of workload i (1-based) is 20070762 + i.
+CONFIG_SEEDS = {i: 20070762 + i for i in range(1, 6)}
+
+
+@dataclasses.dataclass
+class Pair:
+    """One registration problem: align source P onto target Q.
+
+    P, Q: float32 [M,3], [N,3]. normals: float32 [N,3] unit normals of Q (or None).
+    R_gt, t_gt: float64 ground-truth motion taking P onto Q (x -> R_gt x + t_gt).
+    diag: bounding-box diagonal of the clean target surface.
+    """
+    P: np.ndarray
+    Q: np.ndarray
+    normals: np.ndarray | None
+    R_gt: np.ndarray
+    t_gt: np.ndarray
+    diag: float
+    name: str = ""
+
+    @property
+    def M(self) -> int:
+        return int(self.P.shape[0])
+
+    @property
+    def N(self) -> int:
+        return int(self.Q.shape[0])
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+def random_rigid(g: np.random.Generator, max_angle_deg: float, max_trans: float):
+    """Axis uniform on S^2, angle uniform in [0, max_angle], translation uniform per axis."""
+    axis = g.standard_normal(3)
+    axis /= np.linalg.norm(axis)
+    angle = math.radians(max_angle_deg) * g.random()
+    R = Rotation.from_rotvec(axis * angle).as_matrix()
+    t = (2.0 * g.random(3) - 1.0) * max_trans
+    return R, t
+
+
+def _unit(v: np.ndarray) -> np.ndarray:
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+# ----------------------------------------------------------------------------
+# Surfaces. Each sampler draws area-uniform points (rejection on the area
+# element) restricted to a region given by `keep(points) -> bool mask`.
+# ----------------------------------------------------------------------------
+
+def _fill(draw, n: int, keep, g: np.random.Generator):
+    pts, nrm, have = [], [], 0
+    while have < n:
+        x, nx = draw(max(4096, 2 * (n - have)))
+        if keep is not None:
+            mk = keep(x)
+            x, nx = x[mk], nx[mk]
+        pts.append(x)
+        nrm.append(nx)
+        have += x.shape[0]
+    return np.concatenate(pts)[:n], np.concatenate(nrm)[:n]
+
+
+def _torus_draw(g, R=1.0, r=0.4):
+    def draw(n):
+        th = 2 * math.pi * g.random(n)
+        ph = 2 * math.pi * g.random(n)
+        acc = g.random(n) * (R + r) <= (R + r * np.cos(ph))
+        th, ph = th[acc], ph[acc]
+        ring = R + r * np.cos(ph)
+        x = np.stack([ring * np.cos(th), ring * np.sin(th), r * np.sin(ph)], 1)
+        nx = np.stack([np.cos(ph) * np.cos(th), np.cos(ph) * np.sin(th), np.sin(ph)], 1)
+        return x, nx
+    return draw
+
+
+def _height_params(g, bumps=16):
+    return dict(a=g.uniform(-0.15, 0.15, bumps), s=g.uniform(0.05, 0.2, bumps),
+                c=g.random((bumps, 2)))
+
+
+def _height_eval(hp, xy):
+    d = xy[:, None, :] - hp["c"][None]                      # [n,k,2]
+    e = hp["a"] * np.exp(-(d ** 2).sum(-1) / (2 * hp["s"] ** 2))   # [n,k]
+    z = e.sum(1)
+    grad = -(e[..., None] * d / (hp["s"] ** 2)[None, :, None]).sum(1)   # [n,2]
+    return z, grad
+
+
+def _height_draw(g, hp):
+    gx = np.linspace(0, 1, 161)
+    xy = np.stack(np.meshgrid(gx, gx), -1).reshape(-1, 2)
+    _, gr = _height_eval(hp, xy)
+    amax = 1.1 * np.sqrt(1 + (gr ** 2).sum(1)).max()
+
+    def draw(n):
+        xy = g.random((n, 2))
+        z, gr = _height_eval(hp, xy)
+        area = np.sqrt(1 + (gr ** 2).sum(1))
+        acc = g.random(n) * amax <= area
+        xy, z, gr = xy[acc], z[acc], gr[acc]
+        x = np.concatenate([xy, z[:, None]], 1)
+        nx = _unit(np.concatenate([-gr, np.ones((gr.shape[0], 1))], 1))
+        return x, nx
+    return draw
+
+
+def _ellipsoid_params(g, count=8):
+    cen = g.random((count, 3))
+    ax = g.uniform(0.1, 0.3, (count, 3))
+    rot = Rotation.random(count, random_state=g).as_matrix()
+    # quadratic form of ellipsoid k: (x-c)^T A_k (x-c) = 1
+    A = np.einsum("kij,kj,klj->kil", rot, 1.0 / ax ** 2, rot)
+    p = 1.6075   # Knud Thomsen's surface-area approximation, used only as sampling weights
+    a, b, c = ax[:, 0], ax[:, 1], ax[:, 2]
+    area = 4 * math.pi * (((a * b) ** p + (a * c) ** p + (b * c) ** p) / 3) ** (1 / p)
+    return dict(c=cen, ax=ax, rot=rot, A=A, w=area / area.sum())
+
+
+def _ellipsoid_draw(g, ep):
+    cnt = ep["c"].shape[0]
+
+    def draw(n):
+        k = g.choice(cnt, size=n, p=ep["w"])
+        u = _unit(g.standard_normal((n, 3)))
+        ax = ep["ax"][k]
+        dens = np.linalg.norm(u / ax, axis=1) * ax.min(1)
+        acc = g.random(n) <= dens
+        k, u, ax = k[acc], u[acc], ax[acc]
+        x = ep["c"][k] + np.einsum("nij,nj->ni", ep["rot"][k], ax * u)
+        nx = _unit(np.einsum("nij,nj->ni", ep["A"][k], x - ep["c"][k]))
+        # keep only the outer surface of the union
+        d = x[:, None, :] - ep["c"][None]
+        inside = np.einsum("nki,kij,nkj->nk", d, ep["A"], d) < 1.0
+        inside[np.arange(k.size), k] = False
+        ok = ~inside.any(1)
+        return x[ok], nx[ok]
+    return draw
+
+
+# ----------------------------------------------------------------------------
+# Pair assembly
+# ----------------------------------------------------------------------------
+
+def _crop_bounds(g, draw, overlap: float, dim: int):
+    """Two parallel half-spaces with `overlap` of the source inside the target's.
+
+    Target keeps a.x >= s_T, source keeps a.x <= s_S; quantiles chosen so the
+    target and source regions cover the same share of the surface.
+    """
+    if overlap >= 1.0:
+        return None, None
+    a = _unit(g.standard_normal(dim))
+    pool, _ = draw(200_000)
+    v = pool[:, :dim] @ a
+    fs = 1.0 / (2.0 - overlap)
+    s_T = float(np.quantile(v, 1.0 - fs))
+    s_S = float(np.quantile(v, fs))
+    keep_T = lambda x: x[:, :dim] @ a >= s_T
+    keep_S = lambda x: x[:, :dim] @ a <= s_S
+    return keep_T, keep_S
+
+
+def _assemble(g, draw, M, N, overlap, noise, outliers, max_angle, dim_crop, name):
+    keep_T, keep_S = _crop_bounds(g, draw, overlap, dim_crop)
+    Q, nQ = _fill(draw, N, keep_T, g)
+    diag = float(np.linalg.norm(Q.max(0) - Q.min(0)))
+    n_out = int(round(outliers * M))
+    S, _ = _fill(draw, M - n_out, keep_S, g)
+    S = S + noise * diag * g.standard_normal(S.shape)
+    if n_out:
+        lo, hi = S.min(0), S.max(0)
+        S = np.concatenate([S, lo + (hi - lo) * g.random((n_out, 3))])
+    S = S[g.permutation(S.shape[0])]
+    R_s, t_s = random_rigid(g, max_angle, 0.1 * diag)
+    P = S @ R_s.T + t_s
+    return Pair(P=P.astype(np.float32), Q=Q.astype(np.float32),
+                normals=nQ.astype(np.float32), R_gt=R_s.T.copy(),
+                t_gt=-(R_s.T @ t_s), diag=diag, name=name)
+
+
+def torus_pair(seed, M=2000, N=2000, overlap=1.0, noise=0.002, outliers=0.0,
+               max_angle=30.0) -> Pair:
+    g = rng(seed)
+    return _assemble(g, _torus_draw(g), M, N, overlap, noise, outliers, max_angle,
+                     3, "torus")
+
+
+def height_field_pair(seed, M=80_000, N=100_000, overlap=0.6, noise=0.005,
+                      outliers=0.10, max_angle=25.0) -> Pair:
+    g = rng(seed)
+    hp = _height_params(g)
+    return _assemble(g, _height_draw(g, hp), M, N, overlap, noise, outliers,
+                     max_angle, 2, "height_field")
+
+
+def ellipsoid_pair(seed, M=200_000, N=500_000, overlap=0.5, noise=0.003,
+                   outliers=0.05, max_angle=25.0) -> Pair:
+    g = rng(seed)
+    ep = _ellipsoid_params(g)
+    return _assemble(g, _ellipsoid_draw(g, ep), M, N, overlap, noise, outliers,
+                     max_angle, 3, "ellipsoids")
+
+
+def config_pair(i: int, scale: float = 1.0) -> Pair:
+    """The single-pair workloads 1-3 (optionally with M, N scaled down for tests)."""
+    s = CONFIG_SEEDS[i]
+    if i == 1:
+        return torus_pair(s, M=max(8, int(2000 * scale)), N=max(8, int(2000 * scale)))
+    if i == 2:
+        return height_field_pair(s, M=max(8, int(80_000 * scale)), N=max(8, int(100_000 * scale)))
+    if i == 3:
+        return ellipsoid_pair(s, M=max(8, int(200_000 * scale)), N=max(8, int(500_000 * scale)))
+    raise ValueError(f"no single-pair workload {i}")

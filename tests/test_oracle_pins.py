@@ -1,0 +1,391 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test names the passage of the paper it pins and the independent reference:
+a library routine computing the same definition, a closed form, an invariant
+the paper proves, or brute force on tiny inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.spatial.transform import Rotation
+
+import oracle
+
+
+def _rot(g, max_angle=math.pi * 0.9):
+    axis = g.standard_normal(3)
+    axis /= np.linalg.norm(axis)
+    return Rotation.from_rotvec(axis * max_angle * g.random()).as_matrix()
+
+
+# --------------------------------------------------------------------------
+# Correspondence step (Sec. 3 Eq. 3): brute force is the definition.
+# --------------------------------------------------------------------------
+
+def test_closest_matches_dense_argmin_with_ties():
+    g = np.random.default_rng(1)
+    Q = g.random((57, 3))
+    Q[30] = Q[7]                      # duplicate target: tie must go to index 7
+    Q[44] = Q[7]
+    X = np.concatenate([g.random((40, 3)), Q[[7, 12]] + 0.0])
+    idx, d2, d2s = oracle.closest(X, Q)
+    D = ((X[:, None, :] - Q[None]) ** 2).sum(-1)
+    assert np.array_equal(idx, D.argmin(1))        # numpy argmin: first minimum
+    assert np.allclose(d2, D.min(1), rtol=0, atol=1e-15)
+    Ds = np.sort(D, 1)
+    assert np.allclose(d2s, Ds[:, 1], rtol=0, atol=1e-15)
+    assert idx[40] == 7 and d2[40] == 0.0 and d2s[40] == 0.0
+
+
+def test_knn_self_matches_stable_sort():
+    g = np.random.default_rng(2)
+    Q = g.random((80, 3))
+    Q[10] = Q[3]                      # duplicates at distance 0 count
+    idx, d2 = oracle.knn_self(Q, 6)
+    D = ((Q[:, None, :] - Q[None]) ** 2).sum(-1)
+    np.fill_diagonal(D, np.inf)
+    ref = np.argsort(D, axis=1, kind="stable")[:, :6]
+    assert np.array_equal(idx, ref)
+    assert np.allclose(d2, np.take_along_axis(D, ref, 1), rtol=0, atol=1e-15)
+    assert idx[3, 0] == 10 and d2[3, 0] == 0.0
+
+
+# --------------------------------------------------------------------------
+# Alignment step (Eq. 4 and Eq. 12): weighted Procrustes.
+# --------------------------------------------------------------------------
+
+def test_procrustes_recovers_known_motion_exactly():
+    g = np.random.default_rng(3)
+    for _ in range(20):
+        P = g.standard_normal((30, 3))
+        R, t = _rot(g), g.standard_normal(3)
+        w = g.random(30) + 0.01
+        T = oracle.weighted_procrustes(P, P @ R.T + t, w)
+        assert np.abs(T[:3, :3] - R).max() < 1e-12
+        assert np.abs(T[:3, 3] - t).max() < 1e-12
+
+
+def test_procrustes_beats_dense_rotation_search():
+    """The closed form must be at least as good as any rotation on a dense grid."""
+    g = np.random.default_rng(4)
+    P = g.standard_normal((6, 3))
+    Qh = g.standard_normal((6, 3))
+    w = g.random(6)
+    T = oracle.weighted_procrustes(P, Qh, w)
+
+    def cost(R):
+        pbar = (w[:, None] * P).sum(0) / w.sum()
+        qbar = (w[:, None] * Qh).sum(0) / w.sum()
+        r = P @ R.T + (qbar - R @ pbar) - Qh
+        return float((w * (r * r).sum(1)).sum())
+
+    c_closed = cost(T[:3, :3])
+    rots = Rotation.random(40000, random_state=5).as_matrix()
+    costs = np.array([cost(R) for R in rots])
+    best = rots[costs.argmin()]
+    assert c_closed <= costs.min() + 1e-12
+    # local refinement of the sampled best lands on the closed form
+    x = Rotation.from_matrix(best).as_rotvec()
+    for step in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+        for _ in range(200):
+            moved = False
+            for d in np.concatenate([np.eye(3), -np.eye(3)]) * step:
+                c_new = cost(Rotation.from_rotvec(x + d).as_matrix())
+                if c_new < cost(Rotation.from_rotvec(x).as_matrix()):
+                    x, moved = x + d, True
+            if not moved:
+                break
+    assert abs(cost(Rotation.from_rotvec(x).as_matrix()) - c_closed) < 1e-9
+    # and a translation check: t = qbar - R pbar is optimal given R
+    assert np.linalg.det(T[:3, :3]) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_procrustes_rejects_zero_weights():
+    with pytest.raises(oracle.Degenerate):
+        oracle.weighted_procrustes(np.ones((3, 3)), np.ones((3, 3)), np.zeros(3))
+
+
+# --------------------------------------------------------------------------
+# SE(3) exp / log (Eqs. 8-9, App. A).
+# --------------------------------------------------------------------------
+
+def _rodrigues_se3(xi):
+    """Textbook closed form: R = I + sin K + (1-cos) K^2, t = V u (Gallier & Xu)."""
+    w, u = xi[:3], xi[3:]
+    th = np.linalg.norm(w)
+    K = oracle.hat(w / th)
+    R = np.eye(3) + math.sin(th) * K + (1 - math.cos(th)) * K @ K
+    V = np.eye(3) + (1 - math.cos(th)) / th * K + (th - math.sin(th)) / th * K @ K
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = V @ u
+    return T
+
+
+def test_exp_matches_rodrigues_closed_form():
+    g = np.random.default_rng(6)
+    for _ in range(50):
+        xi = np.concatenate([_rot_vec(g), g.standard_normal(3)])
+        T = oracle.se3_exp(oracle.se3_matrix(xi))
+        assert np.abs(T - _rodrigues_se3(xi)).max() < 1e-13
+
+
+def _rot_vec(g, max_angle=3.0):
+    a = g.standard_normal(3)
+    return a / np.linalg.norm(a) * max_angle * g.random()
+
+
+def _log_by_schur(T):
+    """App. A's construction, written from the appendix with scipy's real Schur form.
+
+    R = Q1 D Q1^T with D = diag(D_1, 1); log(U') = [[B, V y], [0, 0]] with
+    B = theta * [[0,-1],[1,0]] on the 2x2 block, y = Q1^T t and
+    V = I - theta/2 K + (1 - theta sin / (2 (1 - cos))) K^2, K the unit generator.
+    """
+    R, t = T[:3, :3], T[:3, 3]
+    D, Q1 = sla.schur(R, output="real")
+    # put the 2x2 rotation block first
+    if abs(D[2, 1]) > abs(D[1, 0]):
+        perm = [1, 2, 0]
+        Q1 = Q1[:, perm]
+        D = Q1.T @ R @ Q1
+    th = math.atan2(D[1, 0] - D[0, 1], D[0, 0] + D[1, 1])
+    K = np.zeros((3, 3))
+    K[0, 1], K[1, 0] = -1.0, 1.0
+    c = 1 - th * math.sin(th) / (2 * (1 - math.cos(th)))
+    V = np.eye(3) - th / 2 * K + c * K @ K
+    L = np.zeros((4, 4))
+    L[:3, :3] = Q1 @ (th * K) @ Q1.T
+    L[:3, 3] = Q1 @ (V @ (Q1.T @ t))
+    return L
+
+
+def test_log_matches_appendix_a_schur_construction():
+    g = np.random.default_rng(7)
+    for _ in range(50):
+        xi = np.concatenate([_rot_vec(g, 3.0) + 1e-3, g.standard_normal(3)])
+        T = oracle.se3_exp(oracle.se3_matrix(xi))
+        L = oracle.se3_log(T)
+        assert np.abs(L - _log_by_schur(T)).max() < 1e-10
+        assert np.abs(oracle.se3_vee(L) - xi).max() < 1e-10      # principal branch, angle < pi
+        assert np.abs(oracle.se3_exp(L) - T).max() < 1e-13
+
+
+def test_log_small_and_zero_angle():
+    T = np.eye(4)
+    T[:3, 3] = [0.3, -0.2, 0.1]
+    assert np.abs(oracle.se3_log(T)[:3, 3] - T[:3, 3]).max() < 1e-15
+    xi = np.array([1e-9, -2e-9, 3e-9, 0.1, 0.2, 0.3])
+    L = oracle.se3_log(oracle.se3_exp(oracle.se3_matrix(xi)))
+    assert np.abs(oracle.se3_vee(L) - xi).max() < 1e-15
+
+
+# --------------------------------------------------------------------------
+# App. D gradient: translation formula and central finite differences.
+# --------------------------------------------------------------------------
+
+def test_appendix_d_translation_formula_equals_exp():
+    g = np.random.default_rng(8)
+    for _ in range(20):
+        d, u = _rot_vec(g), g.standard_normal(3)
+        T = oracle.se3_exp(oracle.se3_matrix(np.concatenate([d, u])))
+        R = T[:3, :3]
+        t = ((R - np.eye(3)) @ oracle.hat(u) @ d + np.outer(d, d) @ u) / (d @ d)
+        assert np.abs(t - T[:3, 3]).max() < 1e-13
+
+
+def _B(xi, P, Qh, Nq):
+    T = oracle.se3_transform(xi)
+    return np.einsum("nd,nd->n", oracle.apply(T, P) - Qh, Nq)
+
+
+@pytest.mark.parametrize("delta_scale", [1.0, 0.3, 1e-3, 1e-7, 0.0])
+def test_plane_gradient_central_differences(delta_scale):
+    g = np.random.default_rng(9)
+    P = g.standard_normal((12, 3))
+    Qh = g.standard_normal((12, 3))
+    Nq = g.standard_normal((12, 3))
+    Nq /= np.linalg.norm(Nq, axis=1, keepdims=True)
+    d = _rot_vec(g, 2.0)
+    d = d / np.linalg.norm(d) * delta_scale if delta_scale else np.zeros(3)
+    u = g.standard_normal(3) if delta_scale else np.zeros(3)   # App. D's delta=0 case is exact at u=0
+    xi = np.concatenate([d, u])
+    J = oracle.plane_gradient(xi, P, Nq)
+    h = 1e-6
+    for j in range(6):
+        e = np.zeros(6)
+        e[j] = h
+        fd = (_B(xi + e, P, Qh, Nq) - _B(xi - e, P, Qh, Nq)) / (2 * h)
+        assert np.abs(J[:, j] - fd).max() < 1e-7 * max(1.0, np.abs(fd).max()), (j, delta_scale)
+
+
+# --------------------------------------------------------------------------
+# Point-to-plane Gauss-Newton sign (Eq. 18): the true motion is a fixed point.
+# --------------------------------------------------------------------------
+
+def test_gauss_newton_fixed_point_and_printed_sign():
+    g = np.random.default_rng(10)
+    Q = g.standard_normal((200, 3))
+    Nq = g.standard_normal((200, 3))
+    Nq /= np.linalg.norm(Nq, axis=1, keepdims=True)
+    xi_true = np.concatenate([_rot_vec(g, 0.5), 0.3 * g.standard_normal(3)])
+    T = oracle.se3_transform(xi_true)
+    P = (Q - T[:3, 3]) @ T[:3, :3]            # R p + t = q exactly
+    B = _B(xi_true, P, Q, Nq)
+    assert np.abs(B).max() < 1e-12
+    J = oracle.plane_gradient(xi_true, P, Nq)
+    A = J.T @ J
+    x_read = np.linalg.solve(A, J.T @ (J @ xi_true - B))      # the reading
+    x_printed = np.linalg.solve(A, J.T @ (B - J @ xi_true))   # as printed
+    assert np.abs(x_read - xi_true).max() < 1e-10
+    assert np.abs(x_printed + xi_true).max() < 1e-10           # lands on -xi
+
+
+# --------------------------------------------------------------------------
+# Anderson acceleration (Eq. 6).
+# --------------------------------------------------------------------------
+
+def test_anderson_lstsq_matches_numpy():
+    g = np.random.default_rng(11)
+    for mk in range(1, 6):
+        dF = g.standard_normal((16, mk))
+        F = g.standard_normal(16)
+        th = oracle.anderson_theta(F, dF)
+        ref = np.linalg.lstsq(dF, F, rcond=None)[0]
+        assert np.abs(th - ref).max() < 1e-12
+
+
+def test_anderson_rank_rule():
+    dF = np.ones((6, 2))
+    assert oracle.anderson_theta(np.ones(6), dF) is None
+    assert oracle.anderson_theta(np.ones(6), np.zeros((6, 1))) is None
+
+
+def test_anderson_solves_linear_fixed_point_in_dim_plus_one_steps():
+    """AA with m >= dim on G(x) = A x + b terminates (GMRES equivalence, Walker & Ni 2011)."""
+    g = np.random.default_rng(12)
+    n = 4
+    A = 0.5 * g.standard_normal((n, n)) / math.sqrt(n)
+    b = g.standard_normal(n)
+    x_star = np.linalg.solve(np.eye(n) - A, b)
+    G = lambda x: A @ x + b
+    x = np.zeros(n)
+    Gs, Fs = [G(x)], [G(x) - x]
+    x = Gs[0]
+    for k in range(1, n + 2):
+        Gk = G(x)
+        Gs.append(Gk)
+        Fs.append(Gk - x)
+        mk = min(k, n)
+        dF = np.stack([Fs[-j] - Fs[-j - 1] for j in range(1, mk + 1)], 1)
+        th = oracle.anderson_theta(Fs[-1], dF)
+        x = Gk - sum(th[j - 1] * (Gs[-j] - Gs[-j - 1]) for j in range(1, mk + 1))
+    assert np.abs(x - x_star).max() < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Welsch surrogate (Eq. 11, App. B).
+# --------------------------------------------------------------------------
+
+def test_welsch_surrogate_majorizes():
+    g = np.random.default_rng(13)
+    x = 3 * g.random(10000)
+    y = 3 * g.random(10000)
+    nu = 0.2 + g.random()
+    assert np.all(oracle.welsch_surrogate(x, y, nu) >= oracle.welsch(x, nu) - 1e-15)
+    assert np.abs(oracle.welsch_surrogate(y, y, nu) - oracle.welsch(y, nu)).max() < 1e-15
+    assert np.all(oracle.welsch(x, nu) < 1.0) and np.all(oracle.welsch(x, nu) >= 0.0)
+
+
+# --------------------------------------------------------------------------
+# nu_min rationale (App. C): a planar square grid of spacing h gives E_Q = h.
+# --------------------------------------------------------------------------
+
+def test_nu_min_square_grid():
+    h = 0.01
+    gx = np.arange(40) * h
+    X, Y = np.meshgrid(gx, gx)
+    Q = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], 1)
+    assert oracle.nu_min_point_to_point(Q) == pytest.approx(h / (3 * math.sqrt(3)), rel=1e-12)
+    N = np.tile([0.0, 0.0, 1.0], (Q.shape[0], 1))
+    assert oracle.nu_min_point_to_plane(Q, N) == 0.0
+
+
+# --------------------------------------------------------------------------
+# Whole algorithms: MM monotonicity, safeguard, exact recovery.
+# --------------------------------------------------------------------------
+
+def _surface_pair(seed, n=600, angle=0.3, noise=0.0):
+    g = np.random.default_rng(seed)
+    xy = g.random((n, 2))
+    z = 0.2 * np.sin(3 * xy[:, 0]) * np.cos(2 * xy[:, 1]) + 0.1 * xy[:, 0] ** 2
+    Q = np.stack([xy[:, 0], xy[:, 1], z], 1)
+    gz = np.stack([-0.6 * np.cos(3 * xy[:, 0]) * np.cos(2 * xy[:, 1]) - 0.2 * xy[:, 0],
+                   0.4 * np.sin(3 * xy[:, 0]) * np.sin(2 * xy[:, 1]), np.ones(n)], 1)
+    N = gz / np.linalg.norm(gz, axis=1, keepdims=True)
+    R = Rotation.from_rotvec(angle * np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])).as_matrix()
+    t = np.array([0.05, -0.03, 0.02])
+    P = (Q - t) @ R + noise * g.standard_normal(Q.shape)     # R p + t = q
+    return P.astype(np.float32), Q.astype(np.float32), N.astype(np.float32), R, t
+
+
+@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch"])
+def test_plain_mm_energy_is_monotone(variant):
+    P, Q, _, _, _ = _surface_pair(14, n=500, angle=0.2, noise=0.002)
+    g = np.random.default_rng(14)
+    Qo = np.concatenate([Q, (g.random((100, 3)) * [1, 1, 0.3]).astype(np.float32)])
+    prm = oracle.Params(variant=variant, anderson_m=0, max_iters=60,
+                        nu_max=0.05 if variant == "p2p_welsch" else 0,
+                        nu_min=0.05 if variant == "p2p_welsch" else 0)
+    r = oracle.register(P, Qo, prm)
+    tr = r["trace"]
+    assert len(tr) > 3
+    assert np.all(np.diff(tr) <= 1e-12 * np.abs(tr[:-1]))
+
+
+def test_safeguard_keeps_accepted_energy_monotone():
+    P, Q, _, _, _ = _surface_pair(15, n=500, angle=0.3, noise=0.003)
+    r = oracle.register(P, Q, oracle.Params(variant="p2p", max_iters=100))
+    assert np.all(np.diff(r["trace"]) <= 0.0)
+
+
+def test_safeguard_reverts_bad_anderson_steps(monkeypatch):
+    """With every AA step sabotaged, Alg. 1 reduces to plain MM plus one revert per step."""
+    P, Q, _, _, _ = _surface_pair(16, n=400, angle=0.25, noise=0.002)
+    plain = oracle.register(P, Q, oracle.Params(variant="p2p", anderson_m=0, max_iters=200))
+    monkeypatch.setattr(oracle, "anderson_theta", lambda F, dF: np.full(dF.shape[1], 50.0))
+    bad = oracle.register(P, Q, oracle.Params(variant="p2p", anderson_m=5, max_iters=200))
+    assert bad["iterations"] == plain["iterations"]
+    assert bad["reverts"] == bad["iterations"] - 1 - plain["reverts"]
+    assert bad["aa_accepted"] == 0
+    assert np.abs(bad["R"] - plain["R"]).max() < 1e-12
+    # plain MM moves to exp(log T'), the revert to T' itself: equal up to rounding
+    assert np.allclose(bad["trace"], plain["trace"], rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch", "p2pl_welsch"])
+def test_exact_copy_is_recovered(variant):
+    P, Q, N, R, t = _surface_pair(17, n=800, angle=0.15)
+    r = oracle.register(P, Q, oracle.Params(variant=variant), normals=N)
+    assert r["status"] == "ok"
+    # float32 inputs: the copy is exact only to float32 rounding
+    assert np.abs(r["R"] - R).max() < 1e-5
+    assert np.abs(r["t"] - t).max() < 1e-5
+    if variant == "p2p":
+        assert r["final_energy"] < 1e-9
+
+
+def test_normalization_round_trip():
+    g = np.random.default_rng(18)
+    P, Q = g.random((20, 3)) * 5 + 3, g.random((30, 3)) * 4 - 1
+    nz = oracle.normalization(P, Q)
+    T = np.eye(4)
+    T[:3, :3] = _rot(g)
+    T[:3, 3] = g.standard_normal(3)
+    Tn = nz.T_to_normalized(T)
+    assert np.abs(nz.T_to_original(Tn) - T).max() < 1e-12
+    assert np.abs(oracle.apply(Tn, nz.fwd(P)) - nz.fwd(oracle.apply(T, P))).max() < 1e-12
+    both = np.concatenate([nz.fwd(P), nz.fwd(Q)])
+    assert np.linalg.norm(both.max(0) - both.min(0)) == pytest.approx(1.0, rel=1e-14)
