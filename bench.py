@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Throughput of the registration hot path in correspondence queries per second.
+
+Workload: Welsch-robust point-to-point ICP with Anderson acceleration (m = 5) and
+the paper's nu schedule (Alg. 1), on a seeded sum-of-Gaussian-bumps height field:
+N = 100,000 target points, M = 80,000 source points cropped to 60% overlap, noise
+0.005 x diagonal, 10% uniform outliers, random rigid motion (angle <= 25 deg,
+translation <= 0.1 x diagonal), identity start. Synthetic inputs stand in for the
+paper's scans.
+
+One step = one whole registration through the C ABI: target index build and
+nu_min statistic, source preparation, the nu_max pass, and every fused
+iteration until the last nu stage converges. Metric = M x iterations / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs independent replicas, one per rank (weak scaling), launched by
+torch.distributed.run. --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import pathlib
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "corr. queries/s (M x iters/s)"
+UNIT = "queries/s"
+VARIANT = "p2p_welsch"
+WORKLOAD = "welsch_p2p_aa_height_field_N100000_M80000"
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+CPU_SAMPLE_M = 40000                # cpu_baseline sample: half the source points, full target
+CPU_SAMPLE_ITERS = 5
+REF_SAMPLE_M = 16000                # --impl reference: 20% of the source points per step
+STEP_SOURCES = ["step.cu", "fricp_internal.cuh", "solver.cuh", "linalg.cuh", "select.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_pair():
+    from paper_2007_07627_gb300 import synth
+    return synth.config_pair(2)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# --------------------------------------------------------------------------
+
+def oracle_sample(pair, nu, iters=CPU_SAMPLE_ITERS, m=CPU_SAMPLE_M):
+    """Alg. 1 of the FP64 oracle on a fixed 20% sample of the source points
+    against the full target, one nu stage, `iters` inner iterations."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    g = np.random.default_rng(20070762)
+    sel = np.sort(g.choice(pair.M, m, replace=False))
+    prm = oracle.Params(variant=VARIANT, max_iters=iters, nu_max=nu, nu_min=nu)
+    t0 = time.perf_counter()
+    r = oracle.register(pair.P[sel], pair.Q, prm)
+    dt = time.perf_counter() - t0
+    return {"value": m * r["iterations"] / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "seconds": dt, "iterations": r["iterations"],
+            "sample": f"FP64 oracle (exhaustive closest point, OpenMP), Alg. 1 on {m} of the {pair.M} source "
+                      f"points vs the full {pair.N}-point target, one nu stage at nu={nu:.3g}, {iters} iterations"}
+
+
+def reference_nu(pair):
+    """nu of the oracle sample: the workload's nu_min (Sec. 4.3), computed by the oracle."""
+    import numpy as np
+
+    import oracle
+    nz = oracle.normalization(pair.P.astype(np.float64), pair.Q.astype(np.float64))
+    return max(oracle.nu_min_point_to_point(nz.fwd(pair.Q.astype(np.float64))), oracle.NU_MIN_FLOOR)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    pair = workload_pair()
+    nu = reference_nu(pair)
+    for _ in range(args.warmup):
+        oracle_sample(pair, nu, iters=1, m=REF_SAMPLE_M)
+    times, its = [], []
+    for _ in range(args.steps):
+        s = oracle_sample(pair, nu, iters=1, m=REF_SAMPLE_M)
+        times.append(s["seconds"])
+        its.append(s["iterations"])
+    value = REF_SAMPLE_M * statistics.mean(its) / statistics.mean(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "variant": VARIANT, "N": pair.N, "M": pair.M},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"each step: Alg. 1 of the FP64 oracle, one iteration, {REF_SAMPLE_M} of "
+                                   f"{pair.M} source points vs the full target, nu={nu:.3g}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU path
+# --------------------------------------------------------------------------
+
+def gpu_selector(local: int) -> str:
+    """nvidia-smi -i argument for CUDA device `local` (UUID when torch exposes it)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[local] if vis else str(local)
+
+
+def measured_peaks():
+    try:
+        return json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+    except (OSError, ValueError):
+        return None
+
+
+def step_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in STEP_SOURCES:
+        h.update((ROOT / "paper_2007_07627_gb300" / "csrc" / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    p = ROOT / "profiles" / "step_kernel_dram.json"
+    try:
+        d = json.loads(p.read_text())
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha256_16") != step_kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2007_07627_gb300 as fr
+
+    pair = workload_pair()
+    Qd = torch.from_numpy(pair.Q).cuda()
+    Pd = torch.from_numpy(pair.P).cuda()
+    prm = fr.params_default(VARIANT)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(q, p):
+        t = fr.target_create(q)
+        r = fr.register(t, p, params=prm)
+        return t, r
+
+    for _ in range(args.warmup):
+        t, r = one_step(Qd, Pd)
+        t.destroy()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    fr.counters(reset=True)
+    clocks = ClockSampler(gpu_selector(local))
+    clocks.start()
+    times, iters, passes = [], [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()                       # evict L2 between timed steps
+        ev0.record()
+        t, r = one_step(Qd, Pd)
+        ev1.record()
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        iters.append(r["iterations"])
+        passes.append(r["corr_passes"])
+        t.destroy()
+    torch.cuda.synchronize()
+    launches = fr.counters(reset=True)["kernel_launches"]
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(tt.item())
+    it = statistics.mean(iters)
+    value = world * pair.M * it / (ms / 1e3)
+
+    # dominant kernel: the fused step, timed launch by launch with CUDA events
+    t = fr.target_create(Qd)
+    rt = fr.register(t, Pd, params=fr.params_default(VARIANT, time_passes=1))
+    t.destroy()
+    per_launch_s = rt["pass_ms"] / 1e3 / rt["device_steps"]
+    algo_bytes = 12 * pair.M + 12 * pair.N
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else 6800.0
+    achieved = algo_bytes / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(), "kernel": "k_step<0> (fused pass + solve)",
+                "avg_launch_us": per_launch_s * 1e6, "algorithmic_bytes_per_launch": algo_bytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+
+    # end to end through the public API with host buffers
+    e2e_t = []
+    fr.counters(reset=True)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        th = fr.target_create(pair.Q)
+        rh = fr.register(th, pair.P, params=prm)
+        e2e_t.append(time.perf_counter() - t0)
+        th.destroy()
+    cnt = fr.counters(reset=True)
+    e2e = {"value": world * pair.M * rh["iterations"] / statistics.mean(e2e_t), "unit": UNIT,
+           "h2d_bytes_per_step": cnt["h2d_bytes"] // args.steps, "d2h_bytes_per_step": cnt["d2h_bytes"] // args.steps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(pair, rt["nu_min"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (candidate distances f32 pairs)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "variant": VARIANT, "N": pair.N, "M": pair.M,
+                   "iterations": it, "corr_passes": statistics.mean(passes), "l2": "flushed between steps",
+                   "step": "target index + nu rules + source prep + all iterations",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * fricp.h -- C ABI of a GB300 (sm_103a) implementation of the per-iteration hot
+ * path of "Fast and Robust Iterative Closest Point" (J. Zhang, Y. Yao, B. Deng;
+ * IEEE TPAMI 2021, arXiv 2007.07627).
+ *
+ * The problem (Sec. 3, Eq. 1): find a rigid motion (R, t) taking the source set
+ * P = {p_i} (M points) onto the target set Q = {q_j} (N points, optionally with
+ * unit normals n_j). Three solvers are provided:
+ *   FRICP_P2P_AA          point-to-point ICP with Anderson acceleration on the
+ *                         se(3) parameterisation and the energy safeguard
+ *                         (Sec. 4.2, "Fast ICP"): Algorithm 1 with psi(x) = x^2,
+ *                         unit weights and a single stage;
+ *   FRICP_P2P_WELSCH_AA   Welsch-robust point-to-point ICP (Sec. 4.3, Alg. 1);
+ *   FRICP_P2PL_WELSCH_AA  Welsch-robust point-to-plane ICP (Sec. 5, Alg. 2).
+ *
+ * Conventions for every call:
+ *   - Point arrays are contiguous float32 [n][3] (x, y, z); normals likewise.
+ *     `on_device` != 0 means the pointer is CUDA device memory of the current
+ *     device, otherwise host memory. The library never keeps a caller pointer
+ *     past the call: inputs are copied into library-owned device buffers.
+ *   - Transforms are double [16], row-major 4x4 homogeneous matrices
+ *     [[R, t], [0, 1]] in the caller's coordinates, x -> R x + t.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). All device work
+ *     of a call is issued on it; calls that return results to the host wait for
+ *     that stream only.
+ *   - No call aborts, traps or exits. Every call returns a fricp_status; on any
+ *     status other than FRICP_OK, fricp_last_error() returns a message
+ *     (thread-local, valid until the next call on the same thread).
+ *   - All calls are thread-compatible: distinct handles may be used from
+ *     distinct threads; one handle must not be used by two threads at once.
+ */
+#ifndef FRICP_H
+#define FRICP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FRICP_OK = 0,
+    FRICP_EINVAL = 1,       /* bad argument: null pointer, size, NaN/Inf input, non-unit normal */
+    FRICP_ENOMEM = 2,       /* device or host allocation failed */
+    FRICP_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error string) */
+    FRICP_ETIMEOUT = 4,     /* the registration did not finish within params.timeout_s or the step budget */
+    FRICP_EDEGENERATE = 5,  /* all Welsch weights vanished (sum w = 0) or the 6x6 point-to-plane
+                               system is not positive definite; the last valid iterate is returned */
+    FRICP_EUNSUPPORTED = 6  /* variant needs something the target lacks (normals) */
+} fricp_status;
+
+typedef enum {
+    FRICP_P2P_AA = 0,
+    FRICP_P2P_WELSCH_AA = 1,
+    FRICP_P2PL_WELSCH_AA = 2
+} fricp_variant;
+
+/* Solver parameters. fricp_params_default fills the paper's defaults. */
+typedef struct {
+    int32_t variant;            /* fricp_variant */
+    int32_t anderson_m;         /* m, previous iterates used by AA: 5 (Sec. 4.2). 0..8; 0 = plain MM */
+    int32_t max_iters;          /* I_nu for point-to-point: 1000 (Sec. 4.3). >= 1 */
+    int32_t p2pl_iters_first;   /* I_nu at nu_max for point-to-plane: 6 (Sec. 5) */
+    int32_t p2pl_iters_cap;     /* +1 per nu stage, at most 10 (Sec. 5) */
+    int32_t max_line_search;    /* l_max of Alg. 2; the paper gives no value: 10 */
+    double  eps;                /* epsilon_nu, convergence threshold: 1e-5 (Sec. 4.3, Sec. 5) */
+    double  nu_max;             /* <= 0: 3 x median initial distance (Sec. 4.3) / plane distance (Sec. 5) */
+    double  nu_min;             /* <= 0: E_Q / (3 sqrt 3) (Sec. 4.3) / H_Q / 6 (Sec. 5) */
+    double  nu_min_floor;       /* lower clamp of nu_min (normalised units): 1e-6 */
+    int32_t steps_per_sync;     /* device steps replayed between two host polls of the done flag: 16 */
+    int32_t use_graph;          /* 1: replay the steps as a captured CUDA graph; 0: plain launches */
+    int32_t time_passes;        /* 1: bracket every step launch with CUDA events (implies use_graph = 0) */
+    int32_t max_steps;          /* hard cap on device steps (correspondence passes): 100000 */
+    double  timeout_s;          /* host wait limit for one registration: 600 */
+} fricp_params;
+
+/* Result of one registration. All transforms in the caller's coordinates. */
+typedef struct {
+    double  R[9];               /* row-major rotation */
+    double  t[3];               /* translation */
+    int32_t status;             /* FRICP_OK or FRICP_EDEGENERATE */
+    int32_t iterations;         /* inner-loop bodies run over all nu stages (Alg. 1 / Alg. 2) */
+    int32_t corr_passes;        /* correspondence computations the algorithm needed */
+    int32_t aa_accepted;        /* Anderson iterates that passed the energy check */
+    int32_t reverts;            /* energy checks that failed (revert in Alg. 1, line search in Alg. 2) */
+    int32_t line_search_trials; /* Alg. 2 line-search evaluations */
+    int32_t stages;             /* nu stages run */
+    int32_t device_steps;       /* fused step kernels that did work (>= corr_passes) */
+    int32_t trace_len;          /* energies written to the caller's trace buffer */
+    int32_t pad0;
+    double  nu_max, nu_min;     /* in normalised units (bounding-box diagonal of P u Q = 1) */
+    double  final_energy;       /* last accepted energy E_prev */
+    double  scale;              /* s of the normalisation x -> s (x - c) */
+    double  center[3];          /* c, the centroid of Q */
+    double  pass_ms;            /* summed device time of step launches when params.time_passes */
+    double  wall_ms;            /* host wall time of the call */
+} fricp_result;
+
+typedef struct fricp_target fricp_target;
+
+/* Fill `out` with the paper's defaults for `variant` (see fricp_params).
+ * Errors: EINVAL for an unknown variant or out == NULL. */
+fricp_status fricp_params_default(int32_t variant, fricp_params *out);
+
+/* Build the target set Q once (Sec. 3: Q is fixed over all iterations): copies
+ * q_xyz (and q_normals if not NULL; they must be unit length within 1e-3) to
+ * the device, builds the exact nearest-neighbour index (Morton-ordered buckets
+ * under a complete bounding-box tree) and the centroid used by the
+ * normalisation. n >= 1. The handle owns all its device memory until
+ * fricp_target_destroy. Errors: EINVAL (bad pointer/size/NaN/non-unit normal),
+ * ENOMEM, ECUDA. */
+fricp_status fricp_target_create(const float *q_xyz, const float *q_normals, int64_t n,
+                                 int32_t on_device, void *stream, fricp_target **out);
+
+/* Release a target (NULL is accepted). Waits for work queued on the target's
+ * creation stream. */
+fricp_status fricp_target_destroy(fricp_target *target);
+
+/* Number of points / whether normals are present. */
+int64_t fricp_target_size(const fricp_target *target);
+int32_t fricp_target_has_normals(const fricp_target *target);
+
+/* Register source P onto the target (Alg. 1 or Alg. 2 of the paper, after the
+ * Sec. 6 normalisation of both sets by one similarity). m >= 1 source points.
+ * T0: initial transform (NULL = identity). trace: optional host buffer receiving
+ * the accepted energy of every inner iteration (Fig. 2), up to trace_capacity
+ * values. Blocks until the result is on the host. Errors: EINVAL, EUNSUPPORTED
+ * (point-to-plane without normals), ENOMEM, ECUDA, ETIMEOUT; EDEGENERATE is
+ * returned in out->status with FRICP_OK as the call status. */
+fricp_status fricp_register(const fricp_target *target, const float *p_xyz, int64_t m,
+                            int32_t on_device, const double *T0, const fricp_params *params,
+                            void *stream, fricp_result *out, double *trace,
+                            int32_t trace_capacity);
+
+/* The correspondence step alone (Sec. 3, Eq. 3): for every x_i = R p_i + t
+ * (T: double[16] row-major, NULL = identity; p_xyz device float32 [m][3]),
+ * the index of its closest target point (original order of Q; ties to the
+ * lowest index) and the squared distance, recomputed in FP64. idx_out and
+ * d2_out are device arrays of m entries. Asynchronous on `stream`.
+ * Errors: EINVAL, ECUDA. */
+fricp_status fricp_closest_points(const fricp_target *target, const float *p_xyz, int64_t m,
+                                  const double *T, int64_t *idx_out, double *d2_out,
+                                  void *stream);
+
+/* One fused correspondence pass at a fixed transform, reduced on the device and
+ * returned to the host: the quantities one iteration of Alg. 1 / Alg. 2 consumes.
+ *   variant P2P_AA / P2P_WELSCH_AA: out[0] = E (sum D_i^2, resp. sum psi_nu(D_i),
+ *     Eq. 1 / Eq. 9), out[1..9] = R' row-major and out[10..12] = t' of the
+ *     alignment step (Eq. 4 / Eq. 12).
+ *   variant P2PL_WELSCH_AA: out[0] = E~ (sum psi_nu(H_i), Eq. 15),
+ *     out[1..6] = xi* = G_ppl(xi) (Eq. 19) for xi = log(T) = [delta; u].
+ * T_normalized (double[16], row-major), nu and every output are in the
+ * normalised coordinates x -> scale (x - center); pass scale = 1 and center =
+ * NULL for the caller's coordinates. p_xyz: float32 [m][3] (host or device per
+ * on_device). Blocks until `out` (16 doubles) is filled. Errors: EINVAL,
+ * EUNSUPPORTED, EDEGENERATE, ENOMEM, ECUDA. */
+fricp_status fricp_eval_pass(const fricp_target *target, const float *p_xyz, int64_t m,
+                             int32_t on_device, int32_t variant, const double *T_normalized,
+                             double nu, double scale, const double *center, void *stream,
+                             double *out);
+
+/* The nu rules alone, in normalised units for the given scale (Sec. 4.3, Sec. 5,
+ * App. C): nu_min from the six nearest neighbours of every target point. */
+fricp_status fricp_target_nu_min(const fricp_target *target, int32_t variant, double scale,
+                                 void *stream, double *nu_min_out);
+
+/* Accounting of the calls made on this thread since the last reset: kernel
+ * launches issued by libfricp (each replayed graph node counts once, and each
+ * radix sort counts the launches it issues) and bytes copied host->device and
+ * device->host. Any pointer may be NULL. reset != 0 zeroes the counters after
+ * reading them. Never fails. */
+void fricp_counters(int64_t *kernel_launches, int64_t *h2d_bytes, int64_t *d2h_bytes, int32_t reset);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *fricp_last_error(void);
+
+/* ABI version: (major << 16) | minor. */
+int32_t fricp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRICP_H */

@@ -1,0 +1,270 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Covers the correspondence step (tie rule), one fused pass (energy and the
+alignment / Gauss-Newton result), the nu rules, whole registrations of all
+three variants (iteration counts, R within 1e-5 rad, t within 1e-6 x diagonal),
+determinism, and the edge cases: one-point and ragged sets, duplicate target
+points, far outliers, a degenerate weight underflow.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_07627_gb300 import synth
+from tests.gpu_common import (R_TOL_RAD, T_TOL_DIAG, assert_nn_parity, oracle_pass_p2p, oracle_pass_p2pl,
+                              random_T, rotation_angle)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fr():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2007_07627_gb300 import build
+    build.build()
+    import paper_2007_07627_gb300 as fr
+    fr.lib()
+    return fr
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+# --------------------------------------------------------------------------
+# Correspondence step
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,M", [(1, 1), (2, 5), (15, 33), (16, 257), (17, 300), (1000, 999), (4099, 2049)])
+def test_closest_points_small_and_ragged(fr, N, M):
+    g = np.random.default_rng(N * 7 + M)
+    Q = g.random((N, 3)).astype(np.float32)
+    P = (g.random((M, 3)) * 1.4 - 0.2).astype(np.float32)
+    t = fr.target_create(Q)
+    for trial in range(3):
+        T = random_T(g, 0.5, 0.2) if trial else np.eye(4)
+        idx, d2 = fr.closest_points(t, _dev(P), T)
+        io, do, dso = oracle.closest(oracle.apply(T, P.astype(float)), Q.astype(float))
+        assert_nn_parity(idx.cpu().numpy(), d2.cpu().numpy(), io, do, dso)
+
+
+def test_closest_points_duplicates_go_to_lowest_index(fr):
+    g = np.random.default_rng(3)
+    Q = g.random((300, 3)).astype(np.float32)
+    Q[200] = Q[17]
+    Q[250] = Q[17]
+    Q[120:140] = Q[40]
+    P = np.concatenate([Q[[17, 200, 250, 40, 130]], g.random((50, 3)).astype(np.float32)])
+    t = fr.target_create(Q)
+    idx, d2 = fr.closest_points(t, _dev(P))
+    idx = idx.cpu().numpy()
+    assert list(idx[:5]) == [17, 17, 17, 40, 40]
+    assert np.all(d2.cpu().numpy()[:5] == 0.0)
+
+
+def test_closest_points_far_outliers(fr):
+    g = np.random.default_rng(4)
+    Q = g.random((5000, 3)).astype(np.float32) * [1, 1, 0.01]
+    P = (g.standard_normal((3000, 3)) * 5).astype(np.float32)
+    t = fr.target_create(Q.astype(np.float32))
+    idx, d2 = fr.closest_points(t, _dev(P))
+    io, do, dso = oracle.closest(P.astype(float), Q.astype(float))
+    assert_nn_parity(idx.cpu().numpy(), d2.cpu().numpy(), io, do, dso)
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+def test_closest_points_workload_sampled(fr, cfg):
+    """Full-size target of each single-pair workload, a sample of the queries
+    (the GPU answers all M, the oracle checks 3000)."""
+    pair = synth.config_pair(cfg)
+    t = fr.target_create(pair.Q)
+    g = np.random.default_rng(cfg)
+    sel = g.choice(pair.M, 3000, replace=False)
+    for T in (np.eye(4), np.linalg.inv(np.vstack([np.hstack([pair.R_gt, pair.t_gt[:, None]]), [0, 0, 0, 1]]))):
+        Tg = np.linalg.inv(T)
+        idx, d2 = fr.closest_points(t, _dev(pair.P), Tg)
+        io, do, dso = oracle.closest(oracle.apply(Tg, pair.P[sel].astype(float)), pair.Q.astype(float))
+        assert_nn_parity(idx.cpu().numpy()[sel], d2.cpu().numpy()[sel], io, do, dso)
+
+
+# --------------------------------------------------------------------------
+# One fused pass
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch", "p2pl_welsch"])
+def test_single_pass_matches_oracle(fr, variant):
+    pair = synth.config_pair(2, 0.05)
+    P, Q = pair.P, pair.Q
+    nz = oracle.normalization(P.astype(float), Q.astype(float))
+    t = fr.target_create(Q, pair.normals)
+    g = np.random.default_rng(5)
+    for trial in range(4):
+        Tn = random_T(g, 0.3, 0.05) if trial else np.eye(4)
+        nu = 0.02 + 0.1 * g.random()
+        out = fr.eval_pass(t, P, variant, Tn, nu=nu, scale=nz.s, center=nz.c)
+        if variant == "p2pl_welsch":
+            E, xs, _ = oracle_pass_p2pl(P, Q, pair.normals, Tn, nu, nz.s, nz.c)
+            assert abs(out[0] - E) <= 1e-10 * max(1.0, abs(E))
+            assert np.abs(out[1:7] - xs).max() <= 1e-9
+        else:
+            E, Tp = oracle_pass_p2p(P, Q, Tn, nu, nz.s, nz.c, variant == "p2p_welsch")
+            assert abs(out[0] - E) <= 1e-10 * max(1.0, abs(E))
+            assert np.abs(out[1:10].reshape(3, 3) - Tp[:3, :3]).max() <= 1e-9
+            assert np.abs(out[10:13] - Tp[:3, 3]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("variant", ["p2p_welsch", "p2pl_welsch"])
+def test_nu_min_matches_oracle(fr, variant):
+    pair = synth.config_pair(2, 0.1)
+    nz = oracle.normalization(pair.P.astype(float), pair.Q.astype(float))
+    t = fr.target_create(pair.Q, pair.normals)
+    got = fr.target_nu_min(t, variant, nz.s)
+    Qn = nz.fwd(pair.Q.astype(float))
+    ref = oracle.nu_min_point_to_point(Qn) if variant == "p2p_welsch" else \
+        oracle.nu_min_point_to_plane(Qn, pair.normals.astype(float))
+    assert got == pytest.approx(ref, rel=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Whole registrations
+# --------------------------------------------------------------------------
+
+def _compare(r_g, r_o, diag):
+    assert r_g["status"] == "OK" and r_o["status"] == "ok"
+    for key in ("iterations", "corr_passes", "stages", "reverts", "aa_accepted", "line_search_trials"):
+        assert r_g[key] == r_o[key], (key, r_g[key], r_o[key])
+    assert rotation_angle(r_g["R"], r_o["R"]) < R_TOL_RAD
+    assert np.abs(r_g["t"] - r_o["t"]).max() < T_TOL_DIAG * diag
+    assert r_g["nu_max"] == pytest.approx(r_o["nu_max"], rel=1e-9)
+    assert r_g["nu_min"] == pytest.approx(r_o["nu_min"], rel=1e-9)
+    assert r_g["final_energy"] == pytest.approx(r_o["final_energy"], rel=1e-7, abs=1e-12)
+    tr = r_g["trace"]
+    assert len(tr) == len(r_o["trace"])
+    assert np.allclose(tr, r_o["trace"], rtol=1e-6, atol=1e-12)
+
+
+CASES = [
+    (1, 1.0, "p2p", dict(max_iters=100)),
+    (1, 1.0, "p2p_welsch", {}),
+    (1, 1.0, "p2pl_welsch", {}),
+    (2, 0.05, "p2p", dict(max_iters=100)),
+    (2, 0.05, "p2p_welsch", {}),
+    (2, 0.05, "p2pl_welsch", {}),
+    (3, 0.01, "p2pl_welsch", {}),
+    (3, 0.01, "p2p_welsch", {}),
+]
+
+
+@pytest.mark.parametrize("cfg,scale,variant,over", CASES)
+def test_registration_matches_oracle(fr, cfg, scale, variant, over):
+    pair = synth.config_pair(cfg, scale)
+    prm_o = oracle.Params(variant=variant, **over)
+    r_o = oracle.register(pair.P, pair.Q, prm_o, normals=pair.normals)
+    t = fr.target_create(pair.Q, pair.normals if variant == "p2pl_welsch" else None)
+    r_g = fr.register(t, pair.P, params=fr.params_default(variant, **over), trace_capacity=5000)
+    _compare(r_g, r_o, pair.diag)
+
+
+def test_registration_device_input_and_host_input_agree(fr):
+    pair = synth.config_pair(2, 0.05)
+    t = fr.target_create(_dev(pair.Q))
+    a = fr.register(t, _dev(pair.P), params=fr.params_default("p2p_welsch"))
+    b = fr.register(t, pair.P, params=fr.params_default("p2p_welsch"))
+    c = fr.register(t, pair.P, params=fr.params_default("p2p_welsch", use_graph=0, steps_per_sync=3))
+    for r in (b, c):
+        assert np.array_equal(a["R"], r["R"]) and np.array_equal(a["t"], r["t"])
+        assert a["iterations"] == r["iterations"] and a["corr_passes"] == r["corr_passes"]
+
+
+def test_exact_copy_is_recovered_by_all_variants(fr):
+    g = np.random.default_rng(9)
+    xy = g.random((3000, 2))
+    z = 0.2 * np.sin(3 * xy[:, 0]) * np.cos(2 * xy[:, 1])
+    Q = np.stack([xy[:, 0], xy[:, 1], z], 1)
+    gz = np.stack([-0.6 * np.cos(3 * xy[:, 0]) * np.cos(2 * xy[:, 1]),
+                   0.4 * np.sin(3 * xy[:, 0]) * np.sin(2 * xy[:, 1]), np.ones(3000)], 1)
+    N = (gz / np.linalg.norm(gz, axis=1, keepdims=True)).astype(np.float32)
+    T = random_T(g, 0.2, 0.05)
+    P = ((Q - T[:3, 3]) @ T[:3, :3]).astype(np.float32)
+    t = fr.target_create(Q.astype(np.float32), N)
+    for v in ("p2p", "p2p_welsch", "p2pl_welsch"):
+        r = fr.register(t, P, params=fr.params_default(v))
+        assert r["status"] == "OK"
+        assert rotation_angle(r["R"], T[:3, :3]) < 1e-5, v
+        assert np.abs(r["t"] - T[:3, 3]).max() < 1e-5, v
+
+
+def test_degenerate_weights_are_reported(fr):
+    """A nu so small that every Welsch weight underflows: sum w = 0."""
+    g = np.random.default_rng(10)
+    Q = g.random((500, 3)).astype(np.float32)
+    P = (g.random((400, 3)) + 3.0).astype(np.float32)
+    t = fr.target_create(Q)
+    prm = fr.params_default("p2p_welsch", nu_max=1e-6, nu_min=1e-6)
+    r_g = fr.register(t, P, params=prm)
+    r_o = oracle.register(P, Q, oracle.Params(variant="p2p_welsch", nu_max=1e-6, nu_min=1e-6))
+    assert r_o["status"] == "degenerate"
+    assert r_g["status"] == "EDEGENERATE"
+    assert np.allclose(r_g["R"], np.eye(3)) and np.allclose(r_g["t"], 0.0, atol=1e-12)
+
+
+def test_registration_is_deterministic(fr):
+    pair = synth.config_pair(2, 0.05)
+    t = fr.target_create(pair.Q, pair.normals)
+    for v in ("p2p_welsch", "p2pl_welsch"):
+        a = fr.register(t, pair.P, params=fr.params_default(v), trace_capacity=3000)
+        b = fr.register(t, pair.P, params=fr.params_default(v), trace_capacity=3000)
+        assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["t"], b["t"])
+        assert np.array_equal(a["trace"], b["trace"])
+
+
+def test_invalid_inputs_are_rejected(fr):
+    Q = np.random.default_rng(1).random((100, 3)).astype(np.float32)
+    bad = Q.copy()
+    bad[5, 1] = np.nan
+    with pytest.raises(fr.FricpError) as e:
+        fr.target_create(bad)
+    assert e.value.status == 1
+    with pytest.raises(fr.FricpError) as e:
+        fr.target_create(_dev(bad))
+    assert e.value.status == 1
+    t = fr.target_create(Q)
+    with pytest.raises(fr.FricpError) as e:
+        fr.register(t, Q, params=fr.params_default("p2pl_welsch"))
+    assert e.value.status == 6
+    with pytest.raises(fr.FricpError) as e:
+        fr.target_create(Q, np.ones((100, 3), np.float32))
+    assert e.value.status == 1
+
+
+def test_workload2_full_size_properties(fr):
+    """Full-size workload 2 in the bench's launch configuration: sampled
+    closest points at the final transform, one full-size pass against the
+    oracle, and the safeguard's monotone accepted energy within each stage."""
+    pair = synth.config_pair(2)
+    t = fr.target_create(pair.Q, pair.normals)
+    r = fr.register(t, pair.P, params=fr.params_default("p2p_welsch"), trace_capacity=100000)
+    assert r["status"] == "OK"
+    T = np.eye(4)
+    T[:3, :3], T[:3, 3] = r["R"], r["t"]
+    g = np.random.default_rng(12)
+    sel = g.choice(pair.M, 4000, replace=False)
+    idx, d2 = fr.closest_points(t, _dev(pair.P), T)
+    io, do, dso = oracle.closest(oracle.apply(T, pair.P[sel].astype(float)), pair.Q.astype(float))
+    assert_nn_parity(idx.cpu().numpy()[sel], d2.cpu().numpy()[sel], io, do, dso)
+    # one full-size pass at the GPU's final transform
+    nz = oracle.Normalization(c=r["center"], s=r["scale"])
+    Tn = np.eye(4)
+    Tn[:3, :3] = r["R"]
+    Tn[:3, 3] = nz.s * (r["R"] @ nz.c + r["t"] - nz.c)
+    out = fr.eval_pass(t, pair.P, "p2p_welsch", Tn, nu=r["nu_min"], scale=nz.s, center=nz.c)
+    E, Tp = oracle_pass_p2p(pair.P, pair.Q, Tn, r["nu_min"], nz.s, nz.c, True)
+    assert abs(out[0] - E) <= 1e-10 * E
+    assert np.abs(out[1:10].reshape(3, 3) - Tp[:3, :3]).max() <= 1e-9
+    # within a stage, accepted energies never increase (the safeguard)
+    tr = r["trace"]
+    assert len(tr) == r["iterations"]
