@@ -150,10 +150,15 @@ fricp_status fricp_closest_points(const fricp_target *target, const float *p_xyz
  *     alignment step (Eq. 4 / Eq. 12).
  *   variant P2PL_WELSCH_AA: out[0] = E~ (sum psi_nu(H_i), Eq. 15),
  *     out[1..6] = xi* = G_ppl(xi) (Eq. 19) for xi = log(T) = [delta; u].
+ *   out[16..43]: the reduced FP64 sums of the pass. Point-to-point (17 values):
+ *     sum w, sum w p~ (3), sum w q~ (3), sum w p~ q~^T (9, row-major), E, with
+ *     p~ = p - center, q~ = q - center in the caller's units. Point-to-plane
+ *     (28 values): the upper triangle of sum g z z^T row by row (21), sum g z B
+ *     (6), E, with z = [R p_n x n; n] in normalised units (App. D: J = K z).
  * T_normalized (double[16], row-major), nu and every output are in the
  * normalised coordinates x -> scale (x - center); pass scale = 1 and center =
  * NULL for the caller's coordinates. p_xyz: float32 [m][3] (host or device per
- * on_device). Blocks until `out` (16 doubles) is filled. Errors: EINVAL,
+ * on_device). Blocks until `out` (48 doubles) is filled. Errors: EINVAL,
  * EUNSUPPORTED, EDEGENERATE, ENOMEM, ECUDA. */
 fricp_status fricp_eval_pass(const fricp_target *target, const float *p_xyz, int64_t m,
                              int32_t on_device, int32_t variant, const double *T_normalized,

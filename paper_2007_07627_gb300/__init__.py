@@ -236,7 +236,7 @@ def closest_points(target: Target, p, T=None, stream=None):
 
 
 def eval_pass(target: Target, p, variant, T_normalized, nu=1.0, scale=1.0, center=None, stream=None):
-    """fricp_eval_pass: energy and alignment / Gauss-Newton result of one pass (16 doubles)."""
+    """fricp_eval_pass: energy, alignment / Gauss-Newton result and reduced sums of one pass (48 doubles)."""
     if isinstance(variant, str):
         variant = VARIANTS[variant]
     pp, m, dev, pk = _points(p)
@@ -245,7 +245,7 @@ def eval_pass(target: Target, p, variant, T_normalized, nu=1.0, scale=1.0, cente
     if center is not None:
         ca = np.ascontiguousarray(np.asarray(center, dtype=np.float64))
         c = ca.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    out = np.zeros(16, np.float64)
+    out = np.zeros(48, np.float64)
     _check(lib().fricp_eval_pass(target.handle, pp, m, dev, int(variant), Tp, float(nu), float(scale), c,
                                  _stream(stream), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out

@@ -427,7 +427,8 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     DevBuf<float4> src;
     DevBuf<PairState> st_dev;
     DevBuf<double> partial, resid, trace_dev;
-    if (src.alloc(m, s) != cudaSuccess || st_dev.alloc(1, s) != cudaSuccess ||
+    DevBuf<int> prev;
+    if (src.alloc(m, s) != cudaSuccess || st_dev.alloc(1, s) != cudaSuccess || prev.alloc(m, s) != cudaSuccess ||
         partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
         resid.alloc(robust ? m : 1, s) != cudaSuccess || trace_dev.alloc(trace_capacity, s) != cudaSuccess)
         return fail(FRICP_ENOMEM, "device allocation for the registration");
@@ -470,11 +471,14 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     e = cudaMemcpyAsync(st_dev.p, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the solver state");
     counters().h2d += sizeof(h);
+    e = cudaMemsetAsync(prev.p, 0xff, sizeof(int) * m, s);   // no correspondence yet
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the correspondence buffer");
 
     fricp::StepArgs a;
     a.st = st_dev.p;
     a.ix = fricp::Index{t->d.pts, t->d.nrm, t->d.nodes, (int)t->d.n, t->d.L};
     a.src = src.p;
+    a.prev = prev.p;
     a.partial = partial.p;
     a.resid = resid.p;
     a.trace = trace_capacity > 0 ? trace_dev.p : nullptr;
@@ -482,7 +486,7 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     double pass_ms = 0.0;
     st = run_steps(a, prm.variant, ntiles, prm, s, st_dev.p, &leak, &pass_ms);
     if (leak) {
-        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = true;
+        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = true;
         p.owned = nullptr;
     }
     if (st != FRICP_OK && st != FRICP_ETIMEOUT) return st;
@@ -544,7 +548,8 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     DevBuf<float4> src;
     DevBuf<PairState> st_dev;
     DevBuf<double> partial, Tdev;
-    if (src.alloc(m, s) != cudaSuccess || st_dev.alloc(1, s) != cudaSuccess ||
+    DevBuf<int> prev;
+    if (src.alloc(m, s) != cudaSuccess || st_dev.alloc(1, s) != cudaSuccess || prev.alloc(m, s) != cudaSuccess ||
         partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess || Tdev.alloc(12, s) != cudaSuccess)
         return fail(FRICP_ENOMEM, "device allocation");
     float plo[3], phi[3];
@@ -563,12 +568,14 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
         T12[9 + r] = T_normalized[4 * r + 3];
     }
     e = cudaMemcpyAsync(st_dev.p, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(prev.p, 0xff, sizeof(int) * m, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(Tdev.p, T12, sizeof(T12), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = fricp::launch_setup_eval_xi(st_dev.p, Tdev.p, s);
     fricp::StepArgs a;
     a.st = st_dev.p;
     a.ix = fricp::Index{t->d.pts, t->d.nrm, t->d.nodes, (int)t->d.n, t->d.L};
     a.src = src.p;
+    a.prev = prev.p;
     a.partial = partial.p;
     a.resid = nullptr;
     a.trace = nullptr;
@@ -577,7 +584,7 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, st_dev.p, sizeof(r), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "evaluation pass");
-    for (int i = 0; i < 16; ++i) out[i] = r.eval_out[i];
+    for (int i = 0; i < 48; ++i) out[i] = r.eval_out[i];
     if (r.status == FRICP_EDEGENERATE) return fail(FRICP_EDEGENERATE, "degenerate alignment problem");
     return FRICP_OK;
 }

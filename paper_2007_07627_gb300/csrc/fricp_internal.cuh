@@ -99,28 +99,53 @@ struct PairState {
     // counters
     int iterations, corr_passes, aa_accepted, reverts, ls_trials, stages, device_steps, trace_len;
     double final_energy;
-    double eval_out[16];    // PH_EVAL result
+    double eval_out[48];    // PH_EVAL result: E, T' or xi*, then the reduced sums
 };
 
 struct StepArgs {
     PairState *st;
     Index ix;
     const float4 *src;     // M sorted source points
+    int *prev;             // M: correspondence (sorted target index) of the last pass, -1 if none
     double *partial;       // ntiles * kMaxSums
     double *resid;         // M per-point residuals (PH_INIT)
     double *trace;         // trace_cap energies
 };
 
 // ---------------------------------------------------------------------------
-// Exact nearest neighbour (Sec. 3, Eq. 3) over the bucket tree.
+// Exact nearest neighbour (Sec. 3, Eq. 3) over the bucket tree, one warp at a time.
 //
-// x is the transformed source point in FP64. It is split once into
-// xh = fl32(x), xl = fl32(x - xh); every candidate difference is formed as
-// (xh - q) + xl in float, which carries x to about 2^-48 relative and rounds
-// only relative to the difference itself, so the squared distance of every
-// candidate has a relative error of a few float ulps even when x is far from
-// the origin. Ties in the float distance go to the lowest original index.
+// The 32 lanes of a warp hold 32 consecutive Morton-ordered source points, so
+// their queries are spatially coherent. The warp walks the tree together: a
+// node is entered when any lane's box distance passes that lane's bound (a
+// ballot), the stack is warp-uniform (shared memory), and the points of a
+// bucket are broadcast to all lanes. Nothing diverges but a predicated update.
+//
+// Precision: x is FP64. It is split once into xh = fl32(x), xl = fl32(x - xh);
+// a candidate's difference (xh - q) + xl is formed in float, so its float
+// squared distance has a relative error of a few float ulps (< 4e-7) however
+// far x is from the origin. Every candidate whose float distance is within
+// 2e-6 of the running float bound is re-ranked with its exact FP64 distance,
+// and the winner is the lexicographic minimum of (FP64 d^2, original index): the
+// FP64 argmin with ties to the lowest index. The bucket-pruning bound keeps a
+// 4e-6 slack, so a bucket that may hold the FP64 winner is never skipped.
+//
+// Warm start: a lane may start from any target point (the previous pass's
+// correspondence); its distance is a true upper bound, so the result is the
+// same exact argmin, found with far fewer node visits.
 // ---------------------------------------------------------------------------
+constexpr int kWarpStack = 32;
+constexpr float kTieWindow = 1.0f + 2e-6f;
+
+struct NNLane {
+    double x[3];
+    float xh[3], xl[3];
+    float bestf;
+    double best64;
+    int best_j;
+    int best_orig;
+};
+
 __device__ __forceinline__ void split_point(const double x[3], float xh[3], float xl[3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -140,66 +165,95 @@ __device__ __forceinline__ float box_d2(float4 lo, float4 hi, const float xh[3],
     return fmaf(c, c, fmaf(b, b, a * a));
 }
 
-__device__ __forceinline__ int nn_query(const Index &ix, const double x[3]) {
-    float xh[3], xl[3];
-    split_point(x, xh, xl);
-    float best = __int_as_float(0x7f800000);  // +inf
-    int best_j = -1;
-    int best_orig = 0x7fffffff;
-    int stk_node[kStack];
-    float stk_d[kStack];
+__device__ __forceinline__ float cand_d2f(const NNLane &q, float4 p) {
+    const float dx = (q.xh[0] - p.x) + q.xl[0];
+    const float dy = (q.xh[1] - p.y) + q.xl[1];
+    const float dz = (q.xh[2] - p.z) + q.xl[2];
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+__device__ __forceinline__ double cand_d2_64(const NNLane &q, float4 p) {
+    const double dx = q.x[0] - (double)p.x, dy = q.x[1] - (double)p.y, dz = q.x[2] - (double)p.z;
+    return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ void nn_init(NNLane &q, const double x[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q.x[a] = x[a];
+    split_point(x, q.xh, q.xl);
+    q.bestf = __int_as_float(0x7f800000);
+    q.best64 = __longlong_as_double(0x7ff0000000000000ll);
+    q.best_j = -1;
+    q.best_orig = 0x7fffffff;
+}
+
+__device__ __forceinline__ void nn_offer(NNLane &q, float4 p, int j) {
+    const float d = cand_d2f(q, p);
+    if (d <= q.bestf * kTieWindow) {
+        const double d64 = cand_d2_64(q, p);
+        const int o = __float_as_int(p.w);
+        if (d64 < q.best64 || (d64 == q.best64 && o < q.best_orig)) {
+            q.best64 = d64;
+            q.best_j = j;
+            q.best_orig = o;
+        }
+        q.bestf = fminf(q.bestf, d);
+    }
+}
+
+// stk: kWarpStack ints of shared memory owned by this warp. All 32 lanes must call.
+__device__ __forceinline__ void warp_nn(const Index &ix, bool active, NNLane &q, int *stk) {
+    const unsigned FULL = 0xffffffffu;
+    const unsigned act = __ballot_sync(FULL, active);
+    if (act == 0u) return;
+    const int leader = __ffs(act) - 1;
     int sp = 0;
     int node = 1;
     for (;;) {
         if (node < ix.L) {
             const float4 *b = ix.nodes + 4 * node;
             const float4 lo0 = __ldg(b), hi0 = __ldg(b + 1), lo1 = __ldg(b + 2), hi1 = __ldg(b + 3);
-            float d0 = box_d2(lo0, hi0, xh, xl);
-            float d1 = box_d2(lo1, hi1, xh, xl);
+            const float d0 = box_d2(lo0, hi0, q.xh, q.xl);
+            const float d1 = box_d2(lo1, hi1, q.xh, q.xl);
+            unsigned n0 = __ballot_sync(FULL, active && d0 * kShrink <= q.bestf);
+            unsigned n1 = __ballot_sync(FULL, active && d1 * kShrink <= q.bestf);
             int c0 = 2 * node, c1 = c0 + 1;
-            if (d1 < d0) {
-                const float td = d0; d0 = d1; d1 = td;
+            if (__shfl_sync(FULL, d1 < d0 ? 1 : 0, leader)) {
                 const int tc = c0; c0 = c1; c1 = tc;
+                const unsigned tn = n0; n0 = n1; n1 = tn;
             }
-            if (d0 * kShrink <= best) {
-                if (d1 * kShrink <= best) {
-                    stk_node[sp] = c1;
-                    stk_d[sp] = d1;
-                    ++sp;
-                }
+            if (n0 && n1) {
+                stk[sp] = c1;   // every lane writes the same value
+                __syncwarp();
+                ++sp;
                 node = c0;
                 continue;
             }
+            if (n0) { node = c0; continue; }
+            if (n1) { node = c1; continue; }
         } else {
             const int beg = (node - ix.L) * kLeaf;
             const int end = min(beg + kLeaf, ix.n);
             for (int j = beg; j < end; ++j) {
-                const float4 q = __ldg(ix.pts + j);
-                const float dx = (xh[0] - q.x) + xl[0];
-                const float dy = (xh[1] - q.y) + xl[1];
-                const float dz = (xh[2] - q.z) + xl[2];
-                const float d = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const int orig = __float_as_int(q.w);
-                if (d < best || (d == best && orig < best_orig)) {
-                    best = d;
-                    best_j = j;
-                    best_orig = orig;
-                }
+                const float4 p = __ldg(ix.pts + j);
+                if (active) nn_offer(q, p, j);
             }
         }
         node = 0;
         while (sp > 0) {
             --sp;
-            if (stk_d[sp] * kShrink <= best) {
-                node = stk_node[sp];
+            const int c = stk[sp];
+            const float4 lo = __ldg(ix.nodes + 2 * c), hi = __ldg(ix.nodes + 2 * c + 1);
+            if (__ballot_sync(FULL, active && box_d2(lo, hi, q.xh, q.xl) * kShrink <= q.bestf)) {
+                node = c;
                 break;
             }
         }
         if (node == 0) break;
     }
-    // Only a non-finite x can leave nothing visited; index 0 keeps every read in bounds
-    // and the non-finite distance flows into the sums.
-    return best_j < 0 ? 0 : best_j;
+    // Only a non-finite x can leave a lane without a candidate; index 0 keeps
+    // every read in bounds and the non-finite distance flows into the sums.
+    if (q.best_j < 0) q.best_j = 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -81,18 +81,51 @@ __global__ void k_box_partial(const float *__restrict__ x, const float *__restri
     }
 }
 
+// One block folds the per-block records: thread t takes records t, t+256, ...,
+// then a fixed shared-memory tree (deterministic order).
 __global__ void k_box_final(const BoxPartial *parts, int nparts, BoxPartial *out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    BoxPartial r = parts[0];
-    for (int b = 1; b < nparts; ++b) {
+    __shared__ float slo[3][kRedBlock], shi[3][kRedBlock];
+    __shared__ double ssum[3][kRedBlock];
+    __shared__ int sbad[kRedBlock];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double sm[3] = {0.0, 0.0, 0.0};
+    int bad = 0;
+    for (int b = threadIdx.x; b < nparts; b += kRedBlock) {
         for (int a = 0; a < 3; ++a) {
-            r.lo[a] = fminf(r.lo[a], parts[b].lo[a]);
-            r.hi[a] = fmaxf(r.hi[a], parts[b].hi[a]);
-            r.sum[a] += parts[b].sum[a];
+            lo[a] = fminf(lo[a], parts[b].lo[a]);
+            hi[a] = fmaxf(hi[a], parts[b].hi[a]);
+            sm[a] += parts[b].sum[a];
         }
-        r.bad |= parts[b].bad;
+        bad |= parts[b].bad;
     }
-    *out = r;
+    for (int a = 0; a < 3; ++a) {
+        slo[a][threadIdx.x] = lo[a];
+        shi[a][threadIdx.x] = hi[a];
+        ssum[a][threadIdx.x] = sm[a];
+    }
+    sbad[threadIdx.x] = bad;
+    __syncthreads();
+    for (int s = kRedBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            for (int a = 0; a < 3; ++a) {
+                slo[a][threadIdx.x] = fminf(slo[a][threadIdx.x], slo[a][threadIdx.x + s]);
+                shi[a][threadIdx.x] = fmaxf(shi[a][threadIdx.x], shi[a][threadIdx.x + s]);
+                ssum[a][threadIdx.x] += ssum[a][threadIdx.x + s];
+            }
+            sbad[threadIdx.x] |= sbad[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        BoxPartial r;
+        for (int a = 0; a < 3; ++a) {
+            r.lo[a] = slo[a][0];
+            r.hi[a] = shi[a][0];
+            r.sum[a] = ssum[a][0];
+        }
+        r.bad = sbad[0];
+        *out = r;
+    }
 }
 
 __device__ __forceinline__ unsigned expand_bits10(unsigned v) {
@@ -274,7 +307,7 @@ cudaError_t reduce_box(const float *x, const float *nrm, int64_t n, cudaStream_t
     cudaError_t e = cudaMallocAsync(&parts, sizeof(BoxPartial) * (nb + 1), s);
     if (e != cudaSuccess) return e;
     k_box_partial<<<nb, kRedBlock, 0, s>>>(x, nrm, n, parts);
-    k_box_final<<<1, 32, 0, s>>>(parts, nb, parts + nb);
+    k_box_final<<<1, kRedBlock, 0, s>>>(parts, nb, parts + nb);
     counters().launches += 2;
     BoxPartial h;
     e = cudaMemcpyAsync(&h, parts + nb, sizeof(BoxPartial), cudaMemcpyDeviceToHost, s);

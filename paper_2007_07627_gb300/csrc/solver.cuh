@@ -407,6 +407,8 @@ static __device__ __noinline__ void solver_step(PairState *st, const double *S, 
             ok = align_from_sums(st, S, T);
             for (int i = 0; i < 12; ++i) st->eval_out[1 + i] = T[i];
         }
+        const int K = st->variant == FRICP_P2PL_WELSCH_AA ? kSumsP2PL : kSumsP2P;
+        for (int k = 0; k < K; ++k) st->eval_out[16 + k] = S[k];
         st->status = ok ? FRICP_OK : FRICP_EDEGENERATE;
         st->phase = PH_DONE;
         st->done = 1;

@@ -74,17 +74,37 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
     __syncthreads();
     if (s_done) return;
 
-    double acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    __shared__ int s_stk[kBlock / 32][kWarpStack];
     const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i < s_M) {
-        const float4 p = __ldg(a.src + i);
-        double x[3];
+    const bool active = i < s_M;
+    float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    double x[3] = {0.0, 0.0, 0.0};
+    if (active) {
+        p = __ldg(a.src + i);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
             x[r] = fma(sR[3 * r], (double)p.x, fma(sR[3 * r + 1], (double)p.y, fma(sR[3 * r + 2], (double)p.z, sT[r])));
-        const int j = nn_query(a.ix, x);
+    }
+    NNLane nq;
+    nn_init(nq, x);
+    if (active) {
+        const int j0 = a.prev[i];
+        if (j0 >= 0) {   // warm start from the previous pass's correspondence
+            const float4 q0 = __ldg(a.ix.pts + j0);
+            nq.bestf = cand_d2f(nq, q0);
+            nq.best64 = cand_d2_64(nq, q0);
+            nq.best_j = j0;
+            nq.best_orig = __float_as_int(q0.w);
+        }
+    }
+    warp_nn(a.ix, active, nq, s_stk[threadIdx.x >> 5]);
+
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    if (active) {
+        const int j = nq.best_j;
+        a.prev[i] = j;
         const float4 q = __ldg(a.ix.pts + j);
         const double dx = x[0] - (double)q.x, dy = x[1] - (double)q.y, dz = x[2] - (double)q.z;
         const double s = s_scale;
@@ -158,18 +178,24 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
 }
 
 // Correspondence step alone: index (original order) and FP64 squared distance.
-__global__ void k_closest(Index ix, const float *__restrict__ p, int64_t m, const double *__restrict__ T,
-                          int64_t *__restrict__ idx, double *__restrict__ d2) {
+__global__ void __launch_bounds__(128) k_closest(Index ix, const float *__restrict__ p, int64_t m,
+                                                 const double *__restrict__ T, int64_t *__restrict__ idx,
+                                                 double *__restrict__ d2) {
+    __shared__ int s_stk[128 / 32][kWarpStack];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const double p0 = p[3 * i], p1 = p[3 * i + 1], p2 = p[3 * i + 2];
-    double x[3];
-    for (int r = 0; r < 3; ++r) x[r] = fma(T[3 * r], p0, fma(T[3 * r + 1], p1, fma(T[3 * r + 2], p2, T[9 + r])));
-    const int j = nn_query(ix, x);
-    const float4 q = ix.pts[j];
-    const double dx = x[0] - (double)q.x, dy = x[1] - (double)q.y, dz = x[2] - (double)q.z;
-    idx[i] = __float_as_int(q.w);
-    d2[i] = dx * dx + dy * dy + dz * dz;
+    const bool active = i < m;
+    double x[3] = {0.0, 0.0, 0.0};
+    if (active) {
+        const double p0 = p[3 * i], p1 = p[3 * i + 1], p2 = p[3 * i + 2];
+        for (int r = 0; r < 3; ++r) x[r] = fma(T[3 * r], p0, fma(T[3 * r + 1], p1, fma(T[3 * r + 2], p2, T[9 + r])));
+    }
+    NNLane q;
+    nn_init(q, x);
+    warp_nn(ix, active, q, s_stk[threadIdx.x >> 5]);
+    if (active) {
+        idx[i] = __float_as_int(__ldg(ix.pts + q.best_j).w);
+        d2[i] = q.best64;
+    }
 }
 
 // Single-evaluation set-up for fricp_eval_pass: T is normalised (R, t).

@@ -68,9 +68,9 @@ def test_closest_points_duplicates_go_to_lowest_index(fr):
 
 def test_closest_points_far_outliers(fr):
     g = np.random.default_rng(4)
-    Q = g.random((5000, 3)).astype(np.float32) * [1, 1, 0.01]
+    Q = (g.random((5000, 3)) * [1, 1, 0.01]).astype(np.float32)
     P = (g.standard_normal((3000, 3)) * 5).astype(np.float32)
-    t = fr.target_create(Q.astype(np.float32))
+    t = fr.target_create(Q)
     idx, d2 = fr.closest_points(t, _dev(P))
     io, do, dso = oracle.closest(P.astype(float), Q.astype(float))
     assert_nn_parity(idx.cpu().numpy(), d2.cpu().numpy(), io, do, dso)
@@ -83,7 +83,7 @@ def test_closest_points_workload_sampled(fr, cfg):
     pair = synth.config_pair(cfg)
     t = fr.target_create(pair.Q)
     g = np.random.default_rng(cfg)
-    sel = g.choice(pair.M, 3000, replace=False)
+    sel = g.choice(pair.M, min(3000, pair.M), replace=False)
     for T in (np.eye(4), np.linalg.inv(np.vstack([np.hstack([pair.R_gt, pair.t_gt[:, None]]), [0, 0, 0, 1]]))):
         Tg = np.linalg.inv(T)
         idx, d2 = fr.closest_points(t, _dev(pair.P), Tg)
@@ -115,6 +115,14 @@ def test_single_pass_matches_oracle(fr, variant):
             assert abs(out[0] - E) <= 1e-10 * max(1.0, abs(E))
             assert np.abs(out[1:10].reshape(3, 3) - Tp[:3, :3]).max() <= 1e-9
             assert np.abs(out[10:13] - Tp[:3, 3]).max() <= 1e-9
+            # the reduced sums themselves (reduction step), in the ABI's convention
+            Pn, Qn = nz.fwd(P.astype(float)), nz.fwd(Q.astype(float))
+            idx, d2, _ = oracle.closest(oracle.apply(Tn, Pn), Qn)
+            w = np.exp(-d2 / (2 * nu * nu)) if variant == "p2p_welsch" else np.ones_like(d2)
+            pt, qt = P.astype(float) - nz.c, Q.astype(float)[idx] - nz.c
+            S = np.concatenate([[w.sum()], (w[:, None] * pt).sum(0), (w[:, None] * qt).sum(0),
+                                ((w[:, None] * pt)[:, :, None] * qt[:, None, :]).sum(0).ravel()])
+            assert np.allclose(out[16:32], S, rtol=1e-11, atol=1e-12 * np.abs(S).max())
 
 
 @pytest.mark.parametrize("variant", ["p2p_welsch", "p2pl_welsch"])
