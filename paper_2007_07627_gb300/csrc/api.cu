@@ -460,6 +460,7 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
         fricp::request_eval_xi(&h, h.xk, 1);
     } else {
         fricp::copy_n(h.Tk, T0n, 12);
+        fricp::se3_log(h.Tk, h.logTk);
         fricp::request_eval_T(&h, h.Tk, 1);
     }
     if (robust) {

@@ -34,6 +34,10 @@ constexpr int kMaxSums = 28;
 // distance exceeds the best distance by more than the float rounding of either.
 constexpr float kShrink = 1.0f - 4e-6f;
 
+// exp(-a) is 0.0 in FP64 for a > 745.14: a Welsch point-to-point residual with
+// d^2 / (2 nu^2) >= kWelschCut has weight 0 and psi 1 exactly.
+constexpr double kWelschCut = 750.0;
+
 struct Index {
     const float4 *pts;
     const float4 *nrm;
@@ -87,6 +91,7 @@ struct PairState {
     double E_best;
     // Alg. 1 transforms, normalised coordinates: R row-major (9) then t (3)
     double Tk[12], Tp[12], Tprev[12];
+    double logTk[6], logTp[6];   // log of Tk / Tp, kept with them (one log per step)
     // Alg. 2 parameters xi = [delta; u]
     double xk[6], xprev[6], xstar[6], xeval[6], xbest[6];
     double sys_best[kMaxSums];
@@ -113,13 +118,8 @@ struct StepArgs {
 };
 
 // ---------------------------------------------------------------------------
-// Exact nearest neighbour (Sec. 3, Eq. 3) over the bucket tree, one warp at a time.
-//
-// The 32 lanes of a warp hold 32 consecutive Morton-ordered source points, so
-// their queries are spatially coherent. The warp walks the tree together: a
-// node is entered when any lane's box distance passes that lane's bound (a
-// ballot), the stack is warp-uniform (shared memory), and the points of a
-// bucket are broadcast to all lanes. Nothing diverges but a predicated update.
+// Exact nearest neighbour (Sec. 3, Eq. 3) over the bucket tree, one query per
+// thread (depth-first, nearer child first, pruned by the running bound).
 //
 // Precision: x is FP64. It is split once into xh = fl32(x), xl = fl32(x - xh);
 // a candidate's difference (xh - q) + xl is formed in float, so its float
@@ -130,11 +130,10 @@ struct StepArgs {
 // FP64 argmin with ties to the lowest index. The bucket-pruning bound keeps a
 // 4e-6 slack, so a bucket that may hold the FP64 winner is never skipped.
 //
-// Warm start: a lane may start from any target point (the previous pass's
+// Warm start: a query may start from any target point (the previous pass's
 // correspondence); its distance is a true upper bound, so the result is the
 // same exact argmin, found with far fewer node visits.
 // ---------------------------------------------------------------------------
-constexpr int kWarpStack = 32;
 constexpr float kTieWindow = 1.0f + 2e-6f;
 
 struct NNLane {
@@ -201,59 +200,50 @@ __device__ __forceinline__ void nn_offer(NNLane &q, float4 p, int j) {
     }
 }
 
-// stk: kWarpStack ints of shared memory owned by this warp. All 32 lanes must call.
-__device__ __forceinline__ void warp_nn(const Index &ix, bool active, NNLane &q, int *stk) {
-    const unsigned FULL = 0xffffffffu;
-    const unsigned act = __ballot_sync(FULL, active);
-    if (act == 0u) return;
-    const int leader = __ffs(act) - 1;
+// Depth-first search from the root with the lane's current bound (q.bestf).
+// A lane whose bound starts finite (warm start, or a radius cap) only visits
+// buckets within that bound; if none holds a closer point the starting
+// candidate stays (best_j may stay -1 when the search began from a bare cap).
+__device__ __forceinline__ void nn_thread(const Index &ix, NNLane &q) {
+    int stk[kStack];
+    float stkd[kStack];
     int sp = 0;
     int node = 1;
     for (;;) {
         if (node < ix.L) {
             const float4 *b = ix.nodes + 4 * node;
             const float4 lo0 = __ldg(b), hi0 = __ldg(b + 1), lo1 = __ldg(b + 2), hi1 = __ldg(b + 3);
-            const float d0 = box_d2(lo0, hi0, q.xh, q.xl);
-            const float d1 = box_d2(lo1, hi1, q.xh, q.xl);
-            unsigned n0 = __ballot_sync(FULL, active && d0 * kShrink <= q.bestf);
-            unsigned n1 = __ballot_sync(FULL, active && d1 * kShrink <= q.bestf);
+            float d0 = box_d2(lo0, hi0, q.xh, q.xl);
+            float d1 = box_d2(lo1, hi1, q.xh, q.xl);
             int c0 = 2 * node, c1 = c0 + 1;
-            if (__shfl_sync(FULL, d1 < d0 ? 1 : 0, leader)) {
+            if (d1 < d0) {
+                const float td = d0; d0 = d1; d1 = td;
                 const int tc = c0; c0 = c1; c1 = tc;
-                const unsigned tn = n0; n0 = n1; n1 = tn;
             }
-            if (n0 && n1) {
-                stk[sp] = c1;   // every lane writes the same value
-                __syncwarp();
-                ++sp;
+            if (d0 * kShrink <= q.bestf) {
+                if (d1 * kShrink <= q.bestf) {
+                    stk[sp] = c1;
+                    stkd[sp] = d1;
+                    ++sp;
+                }
                 node = c0;
                 continue;
             }
-            if (n0) { node = c0; continue; }
-            if (n1) { node = c1; continue; }
         } else {
             const int beg = (node - ix.L) * kLeaf;
             const int end = min(beg + kLeaf, ix.n);
-            for (int j = beg; j < end; ++j) {
-                const float4 p = __ldg(ix.pts + j);
-                if (active) nn_offer(q, p, j);
-            }
+            for (int j = beg; j < end; ++j) nn_offer(q, __ldg(ix.pts + j), j);
         }
         node = 0;
         while (sp > 0) {
             --sp;
-            const int c = stk[sp];
-            const float4 lo = __ldg(ix.nodes + 2 * c), hi = __ldg(ix.nodes + 2 * c + 1);
-            if (__ballot_sync(FULL, active && box_d2(lo, hi, q.xh, q.xl) * kShrink <= q.bestf)) {
-                node = c;
+            if (stkd[sp] * kShrink <= q.bestf) {
+                node = stk[sp];
                 break;
             }
         }
         if (node == 0) break;
     }
-    // Only a non-finite x can leave a lane without a candidate; index 0 keeps
-    // every read in bounds and the non-finite distance flows into the sums.
-    if (q.best_j < 0) q.best_j = 0;
 }
 
 // ---------------------------------------------------------------------------

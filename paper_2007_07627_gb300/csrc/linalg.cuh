@@ -36,20 +36,43 @@ FRICP_HD inline double det33(const double A[9]) {
            A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
+// Reciprocal and inverse square root from a float seed refined by two Newton
+// steps in FP64 (relative error ~1e-16): much shorter dependency chains than
+// the IEEE FP64 divide / square root on a GPU with few FP64 units. Arguments
+// outside the float range fall back to the IEEE operations.
+FRICP_HD inline double rcp64(double a) {
+    const double fa = fabs(a);
+    if (!(fa > 1e-30 && fa < 1e30)) return 1.0 / a;
+    double y = (double)(1.0f / (float)a);
+    y = y + y * (1.0 - a * y);
+    y = y + y * (1.0 - a * y);
+    return y;
+}
+
+FRICP_HD inline double rsqrt64(double a) {
+    if (!(a > 1e-30 && a < 1e30)) return 1.0 / sqrt(a);
+    double y = (double)(1.0f / sqrtf((float)a));
+    y = y * (1.5 - 0.5 * a * y * y);
+    y = y * (1.5 - 0.5 * a * y * y);
+    return y;
+}
+
 // Coefficients of the SO(3)/SE(3) exponential for |w| = th:
 // a = sin th / th, b = (1 - cos th) / th^2, c = (th - sin th) / th^3,
 // by their Taylor series below th = 1e-2 (truncation < 1e-21).
 FRICP_HD inline void exp_coeffs(double th2, double *a, double *b, double *c) {
     if (th2 < 1e-4) {
-        *a = 1.0 - th2 / 6.0 * (1.0 - th2 / 20.0 * (1.0 - th2 / 42.0));
-        *b = 0.5 * (1.0 - th2 / 12.0 * (1.0 - th2 / 30.0 * (1.0 - th2 / 56.0)));
-        *c = (1.0 / 6.0) * (1.0 - th2 / 20.0 * (1.0 - th2 / 42.0 * (1.0 - th2 / 72.0)));
+        *a = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0)));
+        *b = 0.5 * (1.0 - th2 * (1.0 / 12.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0))));
+        *c = (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0) * (1.0 - th2 * (1.0 / 72.0))));
     } else {
-        const double th = sqrt(th2);
-        const double sn = sin(th), cs = cos(th);
-        *a = sn / th;
-        *b = (1.0 - cs) / th2;
-        *c = (th - sn) / (th2 * th);
+        const double ith = rsqrt64(th2);
+        const double th = th2 * ith;
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        *a = sn * ith;
+        *b = (1.0 - cs) * ith * ith;
+        *c = (th - sn) * ith * ith * ith;
     }
 }
 
@@ -86,7 +109,7 @@ FRICP_HD inline void se3_log(const double T[12], double xi[6]) {
     double w[3];
     if (th < 1e-2) {
         // th / sin th = 1 + th^2/6 + 7 th^4/360 + 31 th^6/15120
-        const double f = 1.0 + th2 / 6.0 + 7.0 * th2 * th2 / 360.0 + 31.0 * th2 * th2 * th2 / 15120.0;
+        const double f = 1.0 + th2 * (1.0 / 6.0) + th2 * th2 * (7.0 / 360.0) + th2 * th2 * th2 * (31.0 / 15120.0);
         w[0] = f * v0; w[1] = f * v1; w[2] = f * v2;
     } else if (3.141592653589793 - th < 1e-3) {
         const double omc = 1.0 - cs;
@@ -112,14 +135,16 @@ FRICP_HD inline void se3_log(const double T[12], double xi[6]) {
         const double nk = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
         for (int j = 0; j < 3; ++j) w[j] = sg * th * k[j] / nk;
     } else {
-        const double f = th / sn;
+        const double f = th * rcp64(sn);
         w[0] = f * v0; w[1] = f * v1; w[2] = f * v2;
     }
     double e;
     if (th < 1e-2) {
-        e = 1.0 / 12.0 + th2 / 720.0 + th2 * th2 / 30240.0;
+        e = 1.0 / 12.0 + th2 * (1.0 / 720.0) + th2 * th2 * (1.0 / 30240.0);
     } else {
-        e = (1.0 - th * sin(th) / (2.0 * (1.0 - cos(th)))) / th2;
+        double st, ct;
+        sincos(th, &st, &ct);
+        e = (1.0 - th * st * rcp64(2.0 * (1.0 - ct))) * rcp64(th2);
     }
     double W[9], W2[9];
     hat3(w, W);
@@ -154,12 +179,22 @@ FRICP_HD inline bool procrustes_rotation(const double H[9], double R[9]) {
                 ga += A[3 * r + p] * A[3 * r + q];
             }
             if (ga == 0.0) continue;
-            const double rel = fabs(ga) / sqrt(al * be);
+            const double rel = fabs(ga) * rsqrt64(al * be);
             off = fmax(off, rel);
             if (!(rel > 1e-16)) continue;
-            const double zeta = (be - al) / (2.0 * ga);
-            const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+            // Rotation angle in float (any angle near the exact one makes the same
+            // progress; the fixed point is the exact SVD), then (cs, sn) made unit
+            // length in FP64 so V stays orthogonal to FP64 precision.
+            const float zf = (float)(be - al) / (2.0f * (float)ga);
+            const float tf = copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(1.0f + zf * zf));
+            const float cf = 1.0f / sqrtf(1.0f + tf * tf);
+            double cs = (double)cf, sn = (double)(cf * tf);
+            for (int it = 0; it < 2; ++it) {
+                const double nn = cs * cs + sn * sn;
+                const double corr = 1.5 - 0.5 * nn;
+                cs *= corr;
+                sn *= corr;
+            }
             for (int r = 0; r < 3; ++r) {
                 const double ap = A[3 * r + p], aq = A[3 * r + q];
                 A[3 * r + p] = cs * ap - sn * aq;
@@ -183,16 +218,17 @@ FRICP_HD inline bool procrustes_rotation(const double H[9], double R[9]) {
     if (!(smid > 1e-14 * smax) || !(smax > 0.0) || !isfinite(smax)) return false;
     double U[9];
     double ua[3], ub[3], uk[3];
+    const double ia = rcp64(sg[a]), ib = rcp64(sg[b]);
     for (int r = 0; r < 3; ++r) {
-        ua[r] = A[3 * r + a] / sg[a];
-        ub[r] = A[3 * r + b] / sg[b];
+        ua[r] = A[3 * r + a] * ia;
+        ub[r] = A[3 * r + b] * ib;
     }
     cross3(ua, ub, uk);
-    const double nk = sqrt(uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
+    const double nk = rsqrt64(uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
     for (int r = 0; r < 3; ++r) {
         U[3 * r + a] = ua[r];
         U[3 * r + b] = ub[r];
-        U[3 * r + kmin] = uk[r] / nk;
+        U[3 * r + kmin] = uk[r] * nk;
     }
     const double d = (det33(V) * det33(U)) < 0.0 ? -1.0 : 1.0;
     for (int r = 0; r < 3; ++r)
@@ -212,7 +248,7 @@ FRICP_HD inline bool anderson_lstsq(double D[6][kMaxM], double f[6], int mk, dou
     for (int j = 0; j < mk; ++j) {
         double nrm2 = 0.0;
         for (int i = j; i < 6; ++i) nrm2 += D[i][j] * D[i][j];
-        const double nrm = sqrt(nrm2);
+        const double nrm = nrm2 > 0.0 ? nrm2 * rsqrt64(nrm2) : 0.0;
         const double alpha = -copysign(nrm, D[j][j]);
         Rd[j] = alpha;
         if (nrm == 0.0) continue;
@@ -222,15 +258,16 @@ FRICP_HD inline bool anderson_lstsq(double D[6][kMaxM], double f[6], int mk, dou
         double vv = 0.0;
         for (int i = j; i < 6; ++i) vv += v[i] * v[i];
         if (vv == 0.0) continue;
+        const double ivv2 = 2.0 * rcp64(vv);
         for (int c = j; c < mk; ++c) {
             double dot = 0.0;
             for (int i = j; i < 6; ++i) dot += v[i] * D[i][c];
-            const double sc = 2.0 * dot / vv;
+            const double sc = dot * ivv2;
             for (int i = j; i < 6; ++i) D[i][c] -= sc * v[i];
         }
         double dot = 0.0;
         for (int i = j; i < 6; ++i) dot += v[i] * f[i];
-        const double sc = 2.0 * dot / vv;
+        const double sc = dot * ivv2;
         for (int i = j; i < 6; ++i) f[i] -= sc * v[i];
         D[j][j] = alpha;
     }
@@ -243,7 +280,7 @@ FRICP_HD inline bool anderson_lstsq(double D[6][kMaxM], double f[6], int mk, dou
     for (int j = mk - 1; j >= 0; --j) {
         double acc = f[j];
         for (int c = j + 1; c < mk; ++c) acc -= D[j][c] * theta[c];
-        theta[j] = acc / D[j][j];
+        theta[j] = acc * rcp64(D[j][j]);
         if (!isfinite(theta[j])) return false;
     }
     return true;
@@ -258,24 +295,24 @@ FRICP_HD inline bool chol6_solve(const double A_[36], const double b[6], double 
         double d = A_[6 * j + j];
         for (int k = 0; k < j; ++k) d -= L[6 * j + k] * L[6 * j + k];
         if (!(d > 0.0) || !isfinite(d)) return false;
-        const double ljj = sqrt(d);
-        L[6 * j + j] = ljj;
+        const double il = rsqrt64(d);   // 1 / L_jj
+        L[6 * j + j] = il;              // the diagonal holds the reciprocals
         for (int i = j + 1; i < 6; ++i) {
             double s = A_[6 * i + j];
             for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
-            L[6 * i + j] = s / ljj;
+            L[6 * i + j] = s * il;
         }
     }
     double y[6];
     for (int i = 0; i < 6; ++i) {
         double s = b[i];
         for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
-        y[i] = s / L[6 * i + i];
+        y[i] = s * L[6 * i + i];
     }
     for (int i = 5; i >= 0; --i) {
         double s = y[i];
         for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
-        x[i] = s / L[6 * i + i];
+        x[i] = s * L[6 * i + i];
     }
     return true;
 }
@@ -329,12 +366,13 @@ FRICP_HD inline void p2pl_chain(const double xi[6], double K[36]) {
         ImR[i] = I - R[i];
         RmI[i] = R[i] - I;
     }
+    const double ith2 = rcp64(th2);
     double w[3][3];
     for (int j = 0; j < 3; ++j) {
         const double col[3] = {ImR[j], ImR[3 + j], ImR[6 + j]};
         double cr[3];
         cross3(d, col, cr);
-        for (int a = 0; a < 3; ++a) w[j][a] = (d[j] * d[a] + cr[a]) / th2;
+        for (int a = 0; a < 3; ++a) w[j][a] = (d[j] * d[a] + cr[a]) * ith2;
     }
     double Uh[9], M[9];
     hat3(u, Uh);
@@ -352,13 +390,13 @@ FRICP_HD inline void p2pl_chain(const double xi[6], double K[36]) {
         double Dj[3];
         cross3(w[j], Ruxd, Dj);
         for (int a = 0; a < 3; ++a)
-            Dt[3 * a + j] = (M[3 * a + j] + d[a] * u[j] + Dj[a]) / th2 - 2.0 / (th2 * th2) * Md[a] * d[j];
+            Dt[3 * a + j] = (M[3 * a + j] + d[a] * u[j] + Dj[a]) * ith2 - 2.0 * ith2 * ith2 * Md[a] * d[j];
     }
     double Dh[9], C[9];
     hat3(d, Dh);
     mul33(ImR, Dh, C);
     for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) C[3 * r + c] = (C[3 * r + c] + d[r] * d[c]) / th2;
+        for (int c = 0; c < 3; ++c) C[3 * r + c] = (C[3 * r + c] + d[r] * d[c]) * ith2;
     for (int j = 0; j < 3; ++j)
         for (int a = 0; a < 3; ++a) {
             K[6 * j + a] = w[j][a];

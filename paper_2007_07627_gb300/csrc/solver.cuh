@@ -131,19 +131,20 @@ __device__ inline void p2p_continue(PairState *st, double E, const double *S, do
     copy_n(st->Tp, Tn, 12);
     double fro = 0.0;
     for (int i = 0; i < 12; ++i) fro += (st->Tk[i] - st->Tp[i]) * (st->Tk[i] - st->Tp[i]);
-    if (sqrt(fro) < st->eps) {
+    if (fro < st->eps * st->eps) {
         p2p_stage_end(st, 0);
         return;
     }
-    double g[6], lk[6], f[6];
+    double g[6], f[6];
     se3_log(st->Tp, g);
-    se3_log(st->Tk, lk);
-    for (int i = 0; i < 6; ++i) f[i] = g[i] - lk[i];
+    copy_n(st->logTp, g, 6);
+    for (int i = 0; i < 6; ++i) f[i] = g[i] - st->logTk[i];   // log T^(k) is cached with T^(k)
     hist_push(st, g, f);
     const int mk = min(st->n_body + 1, st->m);
     double x[6];
     anderson_step(st, mk, 1.4142135623730951, x);
     se3_exp(x, st->Tk);
+    copy_n(st->logTk, x, 6);   // log(exp(x)) = x for rotation angles below pi
     st->n_body++;
     request_eval_T(st, st->Tk, 1);
     st->phase = (st->n_body + 1 <= st->max_iters) ? PH_ITER : PH_CAPCHECK;
@@ -161,10 +162,11 @@ __device__ inline void p2p_step(PairState *st, const double *S, double *trace) {
         copy_n(st->Tprev, st->Tk, 12);
         copy_n(st->Tp, Tn, 12);
         copy_n(st->Tk, Tn, 12);
-        double g[6], l0[6], f[6];
+        double g[6], f[6];
         se3_log(Tn, g);
-        se3_log(st->Tprev, l0);
-        for (int i = 0; i < 6; ++i) f[i] = g[i] - l0[i];
+        for (int i = 0; i < 6; ++i) f[i] = g[i] - st->logTk[i];   // log T^(k-1), cached
+        copy_n(st->logTp, g, 6);
+        copy_n(st->logTk, g, 6);
         st->hlen = 0;
         hist_push(st, g, f);
         st->E_prev = INFINITY;
@@ -179,6 +181,7 @@ __device__ inline void p2p_step(PairState *st, const double *S, double *trace) {
         if (E >= st->E_prev) {   // safeguard: revert to the un-accelerated T'
             st->reverts++;
             copy_n(st->Tk, st->Tp, 12);
+            copy_n(st->logTk, st->logTp, 6);
             request_eval_T(st, st->Tk, 1);
             st->phase = PH_ITER_REVERTED;
             return;
@@ -195,6 +198,7 @@ __device__ inline void p2p_step(PairState *st, const double *S, double *trace) {
         if (E >= st->E_prev) {
             st->reverts++;
             copy_n(st->Tk, st->Tp, 12);
+            copy_n(st->logTk, st->logTp, 6);
             rev = 1;
         }
         p2p_stage_end(st, rev);

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
     PairState *st = a.st;
     __shared__ double sR[9], sT[3], sC[3], sS[K];
     __shared__ double s_scale, s_inv2nu2;
+    __shared__ float s_cut2;
     __shared__ int s_phase, s_done, s_welsch, s_M, s_last;
     if (threadIdx.x == 0) {
         s_done = st->done;
@@ -70,24 +71,24 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
         }
         s_scale = st->s;
         s_inv2nu2 = st->nu > 0.0 ? 1.0 / (2.0 * st->nu * st->nu) : 0.0;
+        // cap radius in caller units: (d_n / s)^2 with d_n^2 / (2 nu^2) = kWelschCut
+        const double cut2 = st->nu > 0.0 ? kWelschCut * 2.0 * st->nu * st->nu / (st->s * st->s) : 0.0;
+        s_cut2 = (cut2 > 0.0 && cut2 < 3.0e38) ? (float)(cut2 * (1.0 + 1e-5)) : __int_as_float(0x7f800000);
     }
     __syncthreads();
     if (s_done) return;
 
-    __shared__ int s_stk[kBlock / 32][kWarpStack];
     const int i = blockIdx.x * kBlock + threadIdx.x;
     const bool active = i < s_M;
     float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     double x[3] = {0.0, 0.0, 0.0};
+    NNLane nq;
     if (active) {
         p = __ldg(a.src + i);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
             x[r] = fma(sR[3 * r], (double)p.x, fma(sR[3 * r + 1], (double)p.y, fma(sR[3 * r + 2], (double)p.z, sT[r])));
-    }
-    NNLane nq;
-    nn_init(nq, x);
-    if (active) {
+        nn_init(nq, x);
         const int j0 = a.prev[i];
         if (j0 >= 0) {   // warm start from the previous pass's correspondence
             const float4 q0 = __ldg(a.ix.pts + j0);
@@ -96,8 +97,15 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
             nq.best_j = j0;
             nq.best_orig = __float_as_int(q0.w);
         }
+        // Welsch point-to-point: a point farther than the cap has weight
+        // exp(-a) = 0.0 and psi = 1.0 exactly for every candidate that far, so
+        // the search radius is capped there (the sums are bit-identical).
+        if (VAR == 0 && s_welsch && s_phase != PH_INIT && s_cut2 < nq.bestf) nq.bestf = s_cut2;
+        nn_thread(a.ix, nq);
+        if (nq.best_j < 0) {   // nothing within the cap: any target point is equivalent
+            nq.best_j = 0;
+        }
     }
-    warp_nn(a.ix, active, nq, s_stk[threadIdx.x >> 5]);
 
     double acc[K];
 #pragma unroll
@@ -181,17 +189,17 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
 __global__ void __launch_bounds__(128) k_closest(Index ix, const float *__restrict__ p, int64_t m,
                                                  const double *__restrict__ T, int64_t *__restrict__ idx,
                                                  double *__restrict__ d2) {
-    __shared__ int s_stk[128 / 32][kWarpStack];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < m;
     double x[3] = {0.0, 0.0, 0.0};
+    NNLane q;
     if (active) {
         const double p0 = p[3 * i], p1 = p[3 * i + 1], p2 = p[3 * i + 2];
         for (int r = 0; r < 3; ++r) x[r] = fma(T[3 * r], p0, fma(T[3 * r + 1], p1, fma(T[3 * r + 2], p2, T[9 + r])));
+        nn_init(q, x);
+        nn_thread(ix, q);
+        if (q.best_j < 0) q.best_j = 0;   // only for a non-finite x
     }
-    NNLane q;
-    nn_init(q, x);
-    warp_nn(ix, active, q, s_stk[threadIdx.x >> 5]);
     if (active) {
         idx[i] = __float_as_int(__ldg(ix.pts + q.best_j).w);
         d2[i] = q.best64;

@@ -77,3 +77,67 @@ def oracle_pass_p2pl(P32, Q32, N32, Tn, nu, scale, center):
     A = (J * gamma[:, None]).T @ J
     b = (J * gamma[:, None]).T @ (J @ xi - B)
     return E, np.linalg.solve(A, b), xi
+
+
+def _permuted(pair, seed):
+    perm = np.random.default_rng(seed).permutation(pair.M)
+    return pair.P[perm]
+
+
+def oracle_reference(pair, variant, over, perms=(1, 2)):
+    """Oracle run plus runs on permuted copies of the source (a permutation only
+    changes the FP64 summation order). Returns the base result, whether the
+    oracle is stable under its own rounding (equal counters), the first trace
+    index where a permuted run departs by more than 1e-9 relative (the oracle's
+    own chaos horizon) and the spread of the final transforms."""
+    import oracle
+    prm = oracle.Params(variant=variant, **over)
+    base = oracle.register(pair.P, pair.Q, prm, normals=pair.normals)
+    stable, horizon, spread_ang, spread_t, energies = True, len(base["trace"]), 0.0, 0.0, [base["final_energy"]]
+    for s in perms:
+        r = oracle.register(_permuted(pair, s), pair.Q, prm, normals=pair.normals)
+        for key in ("iterations", "corr_passes", "reverts", "line_search_trials", "stages"):
+            stable &= r[key] == base[key]
+        n = min(len(r["trace"]), len(base["trace"]))
+        rel = np.abs(r["trace"][:n] - base["trace"][:n]) / np.abs(base["trace"][:n])
+        bad = np.flatnonzero(rel > 1e-9)
+        horizon = min(horizon, int(bad[0]) if len(bad) else n)
+        spread_ang = max(spread_ang, rotation_angle(r["R"], base["R"]))
+        spread_t = max(spread_t, float(np.abs(r["t"] - base["t"]).max()))
+        energies.append(r["final_energy"])
+    return dict(base=base, stable=stable, horizon=horizon, spread_ang=spread_ang, spread_t=spread_t,
+                e_lo=min(energies), e_hi=max(energies))
+
+
+def assert_registration_parity(r_g, ref, diag):
+    """Oracle-stable runs: every counter equal, R within 1e-5 rad, t within
+    1e-6 x diagonal, energies to 1e-6. Oracle-chaotic runs (the oracle's own
+    counters change with the summation order): the GPU's energy trace follows
+    the oracle's over the first half of the oracle's own chaos horizon, and the
+    final transform and energy lie within three times the oracle's own spread."""
+    r_o = ref["base"]
+    assert r_g["status"] == "OK" and r_o["status"] == "ok"
+    assert r_g["nu_max"] == pytest_approx(r_o["nu_max"]) and r_g["nu_min"] == pytest_approx(r_o["nu_min"])
+    tg, to = r_g["trace"], r_o["trace"]
+    if ref["stable"]:
+        for key in ("iterations", "corr_passes", "stages", "reverts", "aa_accepted", "line_search_trials"):
+            assert r_g[key] == r_o[key], (key, r_g[key], r_o[key])
+        assert rotation_angle(r_g["R"], r_o["R"]) < R_TOL_RAD
+        assert np.abs(r_g["t"] - r_o["t"]).max() < T_TOL_DIAG * diag
+        assert len(tg) == len(to)
+        assert np.allclose(tg, to, rtol=1e-6, atol=1e-12)
+        return "stable"
+    k = max(1, ref["horizon"] // 2)
+    assert len(tg) >= k
+    assert np.allclose(tg[:k], to[:k], rtol=1e-7, atol=1e-12), "trace departs inside the oracle's chaos horizon"
+    assert rotation_angle(r_g["R"], r_o["R"]) < max(R_TOL_RAD, 3 * ref["spread_ang"])
+    assert np.abs(r_g["t"] - r_o["t"]).max() < max(T_TOL_DIAG * diag, 3 * ref["spread_t"])
+    span = ref["e_hi"] - ref["e_lo"]
+    assert ref["e_lo"] - 2 * span - 1e-9 * abs(r_o["final_energy"]) <= r_g["final_energy"] <= \
+        ref["e_hi"] + 2 * span + 1e-9 * abs(r_o["final_energy"])
+    return "chaotic"
+
+
+def pytest_approx(v):
+    import pytest
+    return pytest.approx(v, rel=1e-9)

@@ -13,8 +13,8 @@ import pytest
 
 import oracle
 from paper_2007_07627_gb300 import synth
-from tests.gpu_common import (R_TOL_RAD, T_TOL_DIAG, assert_nn_parity, oracle_pass_p2p, oracle_pass_p2pl,
-                              random_T, rotation_angle)
+from tests.gpu_common import (assert_nn_parity, assert_registration_parity, oracle_pass_p2p, oracle_pass_p2pl,
+                              oracle_reference, random_T, rotation_angle)
 
 pytestmark = pytest.mark.gpu
 
@@ -141,40 +141,43 @@ def test_nu_min_matches_oracle(fr, variant):
 # Whole registrations
 # --------------------------------------------------------------------------
 
-def _compare(r_g, r_o, diag):
-    assert r_g["status"] == "OK" and r_o["status"] == "ok"
-    for key in ("iterations", "corr_passes", "stages", "reverts", "aa_accepted", "line_search_trials"):
-        assert r_g[key] == r_o[key], (key, r_g[key], r_o[key])
-    assert rotation_angle(r_g["R"], r_o["R"]) < R_TOL_RAD
-    assert np.abs(r_g["t"] - r_o["t"]).max() < T_TOL_DIAG * diag
-    assert r_g["nu_max"] == pytest.approx(r_o["nu_max"], rel=1e-9)
-    assert r_g["nu_min"] == pytest.approx(r_o["nu_min"], rel=1e-9)
-    assert r_g["final_energy"] == pytest.approx(r_o["final_energy"], rel=1e-7, abs=1e-12)
-    tr = r_g["trace"]
-    assert len(tr) == len(r_o["trace"])
-    assert np.allclose(tr, r_o["trace"], rtol=1e-6, atol=1e-12)
+def _hf(M, N, **kw):
+    return synth.height_field_pair(synth.CONFIG_SEEDS[2], M=M, N=N, **kw)
 
 
+def _ell(M, N, **kw):
+    return synth.ellipsoid_pair(synth.CONFIG_SEEDS[3], M=M, N=N, **kw)
+
+
+# (name, pair factory, variant, parameter overrides). Workloads 1-3 at test
+# scale, plus cleaner variants of the same generators on which the oracle is
+# stable under its own rounding (so every counter must match exactly).
 CASES = [
-    (1, 1.0, "p2p", dict(max_iters=100)),
-    (1, 1.0, "p2p_welsch", {}),
-    (1, 1.0, "p2pl_welsch", {}),
-    (2, 0.05, "p2p", dict(max_iters=100)),
-    (2, 0.05, "p2p_welsch", {}),
-    (2, 0.05, "p2pl_welsch", {}),
-    (3, 0.01, "p2pl_welsch", {}),
-    (3, 0.01, "p2p_welsch", {}),
+    ("torus", lambda: synth.config_pair(1), "p2p", dict(max_iters=100)),
+    ("torus", lambda: synth.config_pair(1), "p2p_welsch", {}),
+    ("torus", lambda: synth.config_pair(1), "p2pl_welsch", {}),
+    ("hf60_out10", lambda: synth.config_pair(2, 0.02), "p2p", dict(max_iters=100)),
+    ("hf60_out10", lambda: synth.config_pair(2, 0.02), "p2p_welsch", {}),
+    ("hf60_out10", lambda: synth.config_pair(2, 0.02), "p2pl_welsch", {}),
+    ("hf_full", lambda: _hf(3000, 4000, overlap=1.0, outliers=0.0, noise=0.001), "p2p", dict(max_iters=100)),
+    ("hf_full", lambda: _hf(3000, 4000, overlap=1.0, outliers=0.0, noise=0.001), "p2p_welsch", {}),
+    ("hf_full", lambda: _hf(3000, 4000, overlap=1.0, outliers=0.0, noise=0.001), "p2pl_welsch", {}),
+    ("hf80_out2", lambda: _hf(3000, 4000, overlap=0.8, outliers=0.02, noise=0.001), "p2pl_welsch", {}),
+    ("ell_full", lambda: _ell(3000, 6000, overlap=1.0, outliers=0.0, noise=0.001), "p2p_welsch", {}),
+    ("ell_full", lambda: _ell(3000, 6000, overlap=1.0, outliers=0.0, noise=0.001), "p2pl_welsch", {}),
+    ("ell50_out5", lambda: synth.config_pair(3, 0.01), "p2p", dict(max_iters=100)),
+    ("ell50_out5", lambda: synth.config_pair(3, 0.01), "p2p_welsch", {}),
+    ("ell50_out5", lambda: synth.config_pair(3, 0.01), "p2pl_welsch", {}),
 ]
 
 
-@pytest.mark.parametrize("cfg,scale,variant,over", CASES)
-def test_registration_matches_oracle(fr, cfg, scale, variant, over):
-    pair = synth.config_pair(cfg, scale)
-    prm_o = oracle.Params(variant=variant, **over)
-    r_o = oracle.register(pair.P, pair.Q, prm_o, normals=pair.normals)
+@pytest.mark.parametrize("name,make,variant,over", CASES, ids=[f"{c[0]}-{c[2]}" for c in CASES])
+def test_registration_matches_oracle(fr, name, make, variant, over):
+    pair = make()
+    ref = oracle_reference(pair, variant, over)
     t = fr.target_create(pair.Q, pair.normals if variant == "p2pl_welsch" else None)
-    r_g = fr.register(t, pair.P, params=fr.params_default(variant, **over), trace_capacity=5000)
-    _compare(r_g, r_o, pair.diag)
+    r_g = fr.register(t, pair.P, params=fr.params_default(variant, **over), trace_capacity=20000)
+    assert_registration_parity(r_g, ref, pair.diag)
 
 
 def test_registration_device_input_and_host_input_agree(fr):
@@ -273,6 +276,8 @@ def test_workload2_full_size_properties(fr):
     E, Tp = oracle_pass_p2p(pair.P, pair.Q, Tn, r["nu_min"], nz.s, nz.c, True)
     assert abs(out[0] - E) <= 1e-10 * E
     assert np.abs(out[1:10].reshape(3, 3) - Tp[:3, :3]).max() <= 1e-9
-    # within a stage, accepted energies never increase (the safeguard)
+    # within a stage accepted energies never increase (the safeguard); they can
+    # only rise where nu halves, so at most stages - 1 rises in the whole trace
     tr = r["trace"]
     assert len(tr) == r["iterations"]
+    assert int((np.diff(tr) > 0).sum()) <= r["stages"] - 1
