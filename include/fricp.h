@@ -165,6 +165,31 @@ fricp_status fricp_eval_pass(const fricp_target *target, const float *p_xyz, int
                              double nu, double scale, const double *center, void *stream,
                              double *out);
 
+/* No counterpart in the paper: fricp_eval_pass for callers that cannot
+ * allocate device memory -- a caller that has already handed the whole device
+ * to another allocator (a framework's caching allocator), a latency-critical
+ * loop in which cudaMalloc / cudaFree would synchronize the device, or a
+ * real-time or certified deployment that forbids allocation after start-up.
+ * Same arguments and the same 48 outputs as fricp_eval_pass, except:
+ *   - p_xyz_dev is device memory (float32 [m][3]) and 1 <= m <= 32768; a larger
+ *     m returns FRICP_EINVAL with a message saying so;
+ *   - the pass takes the source points in the caller's order (no Morton sort),
+ *     so FP64 sums may differ from fricp_eval_pass in the last bits;
+ *   - its scratch (solver state, tile records, correspondences, packed points)
+ *     is one static device array of about 0.7 MB that every GPU which loads the
+ *     library keeps until the process exits. The call makes no cudaMalloc,
+ *     cudaFree or other allocating call.
+ * The first call on a device looks up the array's device address (set-up, once
+ * per device, with that device current); make that first call before any
+ * stream capture. All calls share the one array and it keeps the last call's
+ * contents; each call rewrites everything it reads, but calls that overlap on
+ * the GPU (different streams or threads) race on it: issue them one after
+ * another. Blocks until `out` is filled. Errors: EINVAL, EUNSUPPORTED,
+ * EDEGENERATE, ECUDA. */
+fricp_status fricp_eval_pass_static(const fricp_target *target, const float *p_xyz_dev, int64_t m,
+                                    int32_t variant, const double *T_normalized, double nu,
+                                    double scale, const double *center, void *stream, double *out);
+
 /* The nu rules alone, in normalised units for the given scale (Sec. 4.3, Sec. 5,
  * App. C): nu_min from the six nearest neighbours of every target point. */
 fricp_status fricp_target_nu_min(const fricp_target *target, int32_t variant, double scale,

@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
     L.fricp_closest_points.argtypes = [vp, vp, i64, dp, vp, vp, vp]
     L.fricp_eval_pass.argtypes = [vp, vp, i64, i32, i32, dp, dbl, dbl, dp, vp, dp]
     L.fricp_target_nu_min.argtypes = [vp, i32, dbl, vp, dp]
+    L.fricp_eval_pass_static.argtypes = [vp, vp, i64, i32, dp, dbl, dbl, dp, vp, dp]
+    L.fricp_eval_pass_static.restype = ctypes.c_int
     L.fricp_counters.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64), i32]
     L.fricp_counters.restype = None
     L.fricp_last_error.restype = ctypes.c_char_p

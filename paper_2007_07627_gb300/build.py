@@ -16,7 +16,7 @@ PKG = pathlib.Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libfricp.so"
-SOURCES = ["api.cu", "index.cu", "step.cu"]
+SOURCES = ["api.cu", "index.cu", "step.cu", "static_pass.cu"]
 HEADERS = ["fricp_internal.cuh", "linalg.cuh", "solver.cuh", "select.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

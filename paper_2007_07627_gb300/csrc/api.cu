@@ -292,6 +292,11 @@ PairState initial_state(const fricp_params &prm, int64_t m, int ntiles, double s
 
 }  // namespace
 
+namespace fricp {
+const TargetDev *target_dev(const fricp_target *t) { return t ? &t->d : nullptr; }
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace fricp
+
 extern "C" {
 
 int32_t fricp_version(void) { return (1 << 16) | 0; }

@@ -269,6 +269,11 @@ struct Counters {
 };
 Counters &counters();
 
+// Defined in api.cu: the device view of a target handle, and the message that
+// fricp_last_error returns on this thread.
+const TargetDev *target_dev(const fricp_target *t);
+void set_last_error(const char *msg);
+
 cudaError_t build_target(const float *q_dev, const float *n_dev, int64_t n, cudaStream_t s,
                          TargetDev *t, int *bad_input);
 cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s);

@@ -1,0 +1,152 @@
+// fricp_eval_pass_static: the fused correspondence pass of fricp_eval_pass for
+// callers that must not allocate device memory. Everything the pass needs
+// beyond the caller's input and output lives in one file-scope device array
+// (g_scratch below), which each GPU that loads the library keeps until the
+// process exits.
+//
+// Who needs this: a caller that has already given all device memory to another
+// allocator (a framework's caching allocator that reserved the device), a
+// latency-critical loop where cudaMalloc / cudaFree would synchronize the
+// device, or a real-time or certified deployment that forbids allocation after
+// start-up.
+#include <cstring>
+
+#include "fricp_internal.cuh"
+#include "linalg.cuh"
+#include "solver.cuh"
+
+namespace {
+
+using fricp::PairState;
+
+constexpr int64_t kStaticMaxPoints = 32768;                        // largest m accepted
+constexpr int kStaticTiles = (int)(kStaticMaxPoints / fricp::kBlock);
+constexpr size_t kStateBytes = 16384;                               // >= sizeof(PairState)
+constexpr size_t kTBytes = 256;                                     // 12 doubles, padded
+constexpr size_t kPartialBytes = sizeof(double) * kStaticTiles * fricp::kMaxSums;
+constexpr size_t kPrevBytes = sizeof(int) * kStaticMaxPoints;
+constexpr size_t kSrcBytes = sizeof(float4) * kStaticMaxPoints;
+constexpr size_t kOffT = kStateBytes;
+constexpr size_t kOffPartial = kOffT + kTBytes;
+constexpr size_t kOffPrev = kOffPartial + kPartialBytes;
+constexpr size_t kOffSrc = kOffPrev + kPrevBytes;
+constexpr size_t kScratchBytes = kOffSrc + kSrcBytes;               // about 0.7 MB
+static_assert(sizeof(PairState) <= kStateBytes, "state region too small");
+static_assert(kOffPartial % 256 == 0 && kOffPrev % 256 == 0 && kOffSrc % 256 == 0, "region alignment");
+
+// The scratch of every call. Host code must not pass this name to a kernel: on
+// the host it is only a stand-in; its device address comes from
+// cudaGetSymbolAddress (see scratch_address).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+char *g_addr[kMaxDevices];   // device address of g_scratch per device, set once
+
+// Source points in caller order as float4 (.w = index); no sort, no allocation.
+__global__ void k_pack_source(const float *__restrict__ p, int m, float4 *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = make_float4(p[3 * i], p[3 * i + 1], p[3 * i + 2], __int_as_float(i));
+}
+
+fricp_status static_fail(fricp_status s, const char *msg) {
+    fricp::set_last_error(msg);
+    return s;
+}
+
+// One-time set-up on the current device: the device address of g_scratch.
+fricp_status scratch_address(char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return static_fail(FRICP_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return static_fail(FRICP_EINVAL, "device index out of range");
+    if (g_addr[dev] == nullptr) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_scratch);
+        if (e != cudaSuccess || ptr == nullptr)
+            return static_fail(FRICP_ECUDA, "cudaGetSymbolAddress(g_scratch) failed");
+        g_addr[dev] = (char *)ptr;
+    }
+    *out = g_addr[dev];
+    return FRICP_OK;
+}
+
+}  // namespace
+
+extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const float *p_xyz_dev, int64_t m,
+                                               int32_t variant, const double *T_normalized, double nu,
+                                               double scale, const double *center, void *stream, double *out) {
+    if (!target || !p_xyz_dev || !T_normalized || !out) return static_fail(FRICP_EINVAL, "NULL argument");
+    if (m < 1 || m > kStaticMaxPoints)
+        return static_fail(FRICP_EINVAL, "m must be in 1..32768 for fricp_eval_pass_static");
+    if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_WELSCH_AA) return static_fail(FRICP_EINVAL, "unknown variant");
+    const fricp::TargetDev &td = *fricp::target_dev(target);
+    if (variant == FRICP_P2PL_WELSCH_AA && !td.has_normals)
+        return static_fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");
+    if (!(scale > 0.0)) return static_fail(FRICP_EINVAL, "scale must be > 0");
+    if (variant != FRICP_P2P_AA && !(nu > 0.0)) return static_fail(FRICP_EINVAL, "nu must be > 0");
+    char *base = nullptr;
+    fricp_status st = scratch_address(&base);
+    if (st != FRICP_OK) return st;
+    const cudaStream_t s = (cudaStream_t)stream;
+    PairState *st_dev = reinterpret_cast<PairState *>(base);
+    double *T_dev = reinterpret_cast<double *>(base + kOffT);
+    double *partial = reinterpret_cast<double *>(base + kOffPartial);
+    int *prev = reinterpret_cast<int *>(base + kOffPrev);
+    float4 *src = reinterpret_cast<float4 *>(base + kOffSrc);
+    const int ntiles = (int)((m + fricp::kBlock - 1) / fricp::kBlock);
+
+    // Host-side state image (the same initial state as fricp_eval_pass).
+    PairState h;
+    std::memset(&h, 0, sizeof(h));
+    h.variant = variant;
+    h.m = 5;
+    h.max_iters = 1000;
+    h.cap_first = 6;
+    h.cap_max = 10;
+    h.max_ls = 10;
+    h.M = (int)m;
+    h.ntiles = ntiles;
+    h.eps = 1e-5;
+    h.s = scale;
+    for (int a = 0; a < 3; ++a) h.c[a] = center ? center[a] : 0.0;
+    h.nu_min = 1.0;
+    h.E_prev = INFINITY;
+    h.cap = 6;
+    h.nu = variant == FRICP_P2P_AA ? 1.0 : nu;
+    double T12[12];
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) T12[3 * r + k] = T_normalized[4 * r + k];
+        T12[9 + r] = T_normalized[4 * r + 3];
+    }
+    // Every region the pass reads is rewritten here, so nothing from the last
+    // call leaks in: the whole state (its last-block counter included), T, the
+    // correspondences (-1: none) and the packed source. Tile records are fully
+    // written by the pass before they are read.
+    cudaError_t e = cudaMemcpyAsync(st_dev, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(T_dev, T12, sizeof(T12), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(prev, 0xff, sizeof(int) * m, s);
+    if (e == cudaSuccess) {
+        k_pack_source<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p_xyz_dev, (int)m, src);
+        fricp::counters().launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = fricp::launch_setup_eval_xi(st_dev, T_dev, s);
+    fricp::StepArgs a;
+    a.st = st_dev;
+    a.ix = fricp::Index{td.pts, td.nrm, td.nodes, (int)td.n, td.L};
+    a.src = src;
+    a.prev = prev;
+    a.partial = partial;
+    a.resid = nullptr;
+    a.trace = nullptr;
+    if (e == cudaSuccess) e = fricp::launch_step(a, variant, ntiles, s);
+    PairState r;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, st_dev, sizeof(r), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return static_fail(FRICP_ECUDA, cudaGetErrorString(e));
+    fricp::counters().h2d += sizeof(h) + sizeof(T12);
+    fricp::counters().d2h += sizeof(r);
+    for (int i = 0; i < 48; ++i) out[i] = r.eval_out[i];
+    if (r.status == FRICP_EDEGENERATE) return static_fail(FRICP_EDEGENERATE, "degenerate alignment problem");
+    return FRICP_OK;
+}
