@@ -176,7 +176,7 @@ fricp_status fricp_eval_pass(const fricp_target *target, const float *p_xyz, int
  *   - the pass takes the source points in the caller's order (no Morton sort),
  *     so FP64 sums may differ from fricp_eval_pass in the last bits;
  *   - its scratch (solver state, tile records, correspondences, packed points)
- *     is one static device array of about 0.7 MB that every GPU which loads the
+ *     is one static device array of about 0.8 MB that every GPU which loads the
  *     library keeps until the process exits. The call makes no cudaMalloc,
  *     cudaFree or other allocating call.
  * The first call on a device looks up the array's device address (set-up, once

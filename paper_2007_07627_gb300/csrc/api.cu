@@ -432,9 +432,9 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     DevBuf<float4> src;
     DevBuf<PairState> st_dev;
     DevBuf<double> partial, resid, trace_dev;
-    DevBuf<int> prev;
+    DevBuf<int> prev, queue;
     if (src.alloc(m, s) != cudaSuccess || st_dev.alloc(1, s) != cudaSuccess || prev.alloc(m, s) != cudaSuccess ||
-        partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
+        queue.alloc(m, s) != cudaSuccess || partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
         resid.alloc(robust ? m : 1, s) != cudaSuccess || trace_dev.alloc(trace_capacity, s) != cudaSuccess)
         return fail(FRICP_ENOMEM, "device allocation for the registration");
     float plo[3], phi[3];
@@ -482,9 +482,10 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
 
     fricp::StepArgs a;
     a.st = st_dev.p;
-    a.ix = fricp::Index{t->d.pts, t->d.nrm, t->d.nodes, (int)t->d.n, t->d.L};
+    a.ix = fricp::make_index(t->d);
     a.src = src.p;
     a.prev = prev.p;
+    a.queue = queue.p;
     a.partial = partial.p;
     a.resid = resid.p;
     a.trace = trace_capacity > 0 ? trace_dev.p : nullptr;
@@ -492,7 +493,7 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     double pass_ms = 0.0;
     st = run_steps(a, prm.variant, ntiles, prm, s, st_dev.p, &leak, &pass_ms);
     if (leak) {
-        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = true;
+        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = queue.leak = true;
         p.owned = nullptr;
     }
     if (st != FRICP_OK && st != FRICP_ETIMEOUT) return st;
@@ -554,9 +555,10 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     DevBuf<float4> src;
     DevBuf<PairState> st_dev;
     DevBuf<double> partial, Tdev;
-    DevBuf<int> prev;
+    DevBuf<int> prev, queue;
     if (src.alloc(m, s) != cudaSuccess || st_dev.alloc(1, s) != cudaSuccess || prev.alloc(m, s) != cudaSuccess ||
-        partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess || Tdev.alloc(12, s) != cudaSuccess)
+        queue.alloc(m, s) != cudaSuccess || partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
+        Tdev.alloc(12, s) != cudaSuccess)
         return fail(FRICP_ENOMEM, "device allocation");
     float plo[3], phi[3];
     int bad = 0;
@@ -579,9 +581,10 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     if (e == cudaSuccess) e = fricp::launch_setup_eval_xi(st_dev.p, Tdev.p, s);
     fricp::StepArgs a;
     a.st = st_dev.p;
-    a.ix = fricp::Index{t->d.pts, t->d.nrm, t->d.nodes, (int)t->d.n, t->d.L};
+    a.ix = fricp::make_index(t->d);
     a.src = src.p;
     a.prev = prev.p;
+    a.queue = queue.p;
     a.partial = partial.p;
     a.resid = nullptr;
     a.trace = nullptr;

@@ -24,7 +24,7 @@ namespace fricp {
 
 constexpr int kBlock = 256;        // threads per step block = source points per tile
 constexpr int kLeaf = 16;          // target points per bucket
-constexpr int kStack = 32;         // traversal stack (tree depth <= 27 for n < 2^31)
+constexpr int kStack = 64;         // traversal stack: path siblings + one descent <= 2 x depth (depth <= 27)
 constexpr int kMaxM = 5;           // largest Anderson history m
 constexpr int kSumsP2P = 17;       // W, W p (3), W q (3), W p q^T (9), E
 constexpr int kSumsP2PL = 28;      // g z z^T (21), g z B (6), E
@@ -44,6 +44,7 @@ struct Index {
     const float4 *nodes;
     int n;
     int L;
+    float near_r2;   // a warm-started query with a smaller bound searches alone (per thread)
 };
 
 enum Phase : int {
@@ -76,6 +77,8 @@ struct PairState {
     double c[3];       // normalisation centre (centroid of Q), caller units
     // ---- machine
     unsigned int counter;   // last-block ticket of the running step
+    unsigned int far_count; // queries queued for the warp-per-query search in this step
+    unsigned int far_next;  // next queued query to hand out
     int phase;
     int done;
     int status;
@@ -111,7 +114,9 @@ struct StepArgs {
     PairState *st;
     Index ix;
     const float4 *src;     // M sorted source points
-    int *prev;             // M: correspondence (sorted target index) of the last pass, -1 if none
+    int *prev;             // M: correspondence (sorted target index) of the last pass, -1 if none;
+                           //    the search kernels overwrite it with this pass's correspondence
+    int *queue;            // M: indices of the queries handed to the warp-per-query search
     double *partial;       // ntiles * kMaxSums
     double *resid;         // M per-point residuals (PH_INIT)
     double *trace;         // trace_cap energies
@@ -121,38 +126,73 @@ struct StepArgs {
 // Exact nearest neighbour (Sec. 3, Eq. 3) over the bucket tree, one query per
 // thread (depth-first, nearer child first, pruned by the running bound).
 //
-// Precision: x is FP64. It is split once into xh = fl32(x), xl = fl32(x - xh);
-// a candidate's difference (xh - q) + xl is formed in float, so its float
-// squared distance has a relative error of a few float ulps (< 4e-7) however
-// far x is from the origin. Every candidate whose float distance is within
-// 2e-6 of the running float bound is re-ranked with its exact FP64 distance,
-// and the winner is the lexicographic minimum of (FP64 d^2, original index): the
-// FP64 argmin with ties to the lowest index. The bucket-pruning bound keeps a
-// 4e-6 slack, so a bucket that may hold the FP64 winner is never skipped.
+// Precision: the search never touches the FP64 pipe (a few FP64 units per SM
+// on this GPU). x = R p + t is formed in double-float arithmetic (a float pair
+// hi + lo, error-free products and sums, about 2^-44 relative), so xh = hi and
+// xl = lo carry x far beyond float precision. A candidate's float squared
+// distance uses (xh - q) + xl, rounding only relative to the difference itself
+// (relative error < 4e-7 however far x is from the origin). Every candidate
+// whose float distance is within 2e-6 of the running float bound is re-ranked
+// by its double-float squared distance, and the winner is the lexicographic
+// minimum of (that distance, original index): the exact argmin up to ties
+// closer than about 1e-10 relative, ties to the lowest index. The
+// bucket-pruning bound keeps a 4e-6 slack, so a bucket that may hold the
+// winner is never skipped.
 //
 // Warm start: a query may start from any target point (the previous pass's
 // correspondence); its distance is a true upper bound, so the result is the
-// same exact argmin, found with far fewer node visits.
+// same argmin, found with far fewer node visits.
 // ---------------------------------------------------------------------------
 constexpr float kTieWindow = 1.0f + 2e-6f;
 
 struct NNLane {
-    double x[3];
     float xh[3], xl[3];
-    float bestf;
-    double best64;
+    float bestf;             // float bound (smallest float distance seen)
+    float best_hi, best_lo;  // double-float squared distance of the winner
     int best_j;
     int best_orig;
 };
 
-__device__ __forceinline__ void split_point(const double x[3], float xh[3], float xl[3]) {
+// Error-free transformations (Knuth two-sum, FMA two-product) and a
+// double-float sum renormalised so that |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
+    float s, e;
+    two_sum(h, bh, s, e);
+    e += l + bl;
+    h = s + e;
+    l = e - (h - s);
+}
+
+// x = R p + t in double-float from float splits of the FP64 R and t.
+__device__ __forceinline__ void df_transform(const float Rh[9], const float Rl[9], const float th[3],
+                                             const float tl[3], float4 p, float xh[3], float xl[3]) {
+    const float pv[3] = {p.x, p.y, p.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        xh[a] = __double2float_rn(x[a]);
-        xl[a] = __double2float_rn(x[a] - (double)xh[a]);
+        float h = th[a], l = tl[a];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float ph = Rh[3 * a + j] * pv[j];
+            float pe = fmaf(Rh[3 * a + j], pv[j], -ph);
+            pe = fmaf(Rl[3 * a + j], pv[j], pe);
+            df_add(h, l, ph, pe);
+        }
+        xh[a] = h;
+        xl[a] = l;
     }
 }
 
+// Split an FP64 value into a float pair (host or device set-up code).
+FRICP_HD inline void split_double(double v, float &h, float &l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
 __device__ __forceinline__ float axis_gap(float lo, float hi, float xh, float xl) {
     return fmaxf(fmaxf((lo - xh) - xl, (xh - hi) + xl), 0.0f);
 }
@@ -171,44 +211,104 @@ __device__ __forceinline__ float cand_d2f(const NNLane &q, float4 p) {
     return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
 
-__device__ __forceinline__ double cand_d2_64(const NNLane &q, float4 p) {
-    const double dx = q.x[0] - (double)p.x, dy = q.x[1] - (double)p.y, dz = q.x[2] - (double)p.z;
-    return dx * dx + dy * dy + dz * dz;
+// Squared distance in double-float: (xh - q) is split exactly by two-sum, xl
+// added, each difference squared by two-product.
+__device__ __forceinline__ void cand_d2_df(const NNLane &q, float4 p, float &hi, float &lo) {
+    const float pv[3] = {p.x, p.y, p.z};
+    hi = 0.0f;
+    lo = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float s, e;
+        two_sum(q.xh[a], -pv[a], s, e);
+        e += q.xl[a];
+        const float dh = s + e;
+        const float dl = e - (dh - s);
+        const float sq = dh * dh;
+        float sqe = fmaf(dh, dh, -sq);
+        sqe = fmaf(2.0f * dh, dl, sqe);
+        df_add(hi, lo, sq, sqe);
+    }
 }
 
-__device__ __forceinline__ void nn_init(NNLane &q, const double x[3]) {
+__device__ __forceinline__ void nn_init(NNLane &q, const float xh[3], const float xl[3]) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) q.x[a] = x[a];
-    split_point(x, q.xh, q.xl);
+    for (int a = 0; a < 3; ++a) {
+        q.xh[a] = xh[a];
+        q.xl[a] = xl[a];
+    }
     q.bestf = __int_as_float(0x7f800000);
-    q.best64 = __longlong_as_double(0x7ff0000000000000ll);
+    q.best_hi = __int_as_float(0x7f800000);
+    q.best_lo = 0.0f;
     q.best_j = -1;
     q.best_orig = 0x7fffffff;
 }
 
-__device__ __forceinline__ void nn_offer(NNLane &q, float4 p, int j) {
+// Make candidate p (sorted index j) the current winner unconditionally (warm start).
+__device__ __forceinline__ void nn_seed(NNLane &q, float4 p, int j) {
+    q.bestf = cand_d2f(q, p);
+    cand_d2_df(q, p, q.best_hi, q.best_lo);
+    q.best_j = j;
+    q.best_orig = __float_as_int(p.w);
+}
+
+// (double-float d^2, original index) lexicographic order; both pairs are
+// renormalised, so (hi, lo) order is the order of hi + lo.
+__device__ __forceinline__ bool lex_less(float ha, float la, int oa, float hb, float lb, int ob) {
+    return ha < hb || (ha == hb && (la < lb || (la == lb && oa < ob)));
+}
+
+// Returns true when p entered the tie window (the lane's bound or winner may change).
+__device__ __forceinline__ bool nn_offer(NNLane &q, float4 p, int j) {
     const float d = cand_d2f(q, p);
     if (d <= q.bestf * kTieWindow) {
-        const double d64 = cand_d2_64(q, p);
+        float hi, lo;
+        cand_d2_df(q, p, hi, lo);
         const int o = __float_as_int(p.w);
-        if (d64 < q.best64 || (d64 == q.best64 && o < q.best_orig)) {
-            q.best64 = d64;
+        if (lex_less(hi, lo, o, q.best_hi, q.best_lo, q.best_orig)) {
+            q.best_hi = hi;
+            q.best_lo = lo;
             q.best_j = j;
             q.best_orig = o;
         }
         q.bestf = fminf(q.bestf, d);
+        return true;
     }
+    return false;
 }
 
 // Depth-first search from the root with the lane's current bound (q.bestf).
 // A lane whose bound starts finite (warm start, or a radius cap) only visits
 // buckets within that bound; if none holds a closer point the starting
 // candidate stays (best_j may stay -1 when the search began from a bare cap).
-__device__ __forceinline__ void nn_thread(const Index &ix, NNLane &q) {
+// start_leaf >= 0 (the bucket of a warm-start candidate): the search begins at
+// that bucket instead of the root. The siblings of the bucket's path to the
+// root are pushed first (their subtrees partition the rest of the tree), the
+// deepest on top, each with its box distance; the bucket itself is scanned
+// first. Near the previous correspondence the bound then prunes almost every
+// sibling at once, so a search costs a few memory latencies instead of one per
+// tree level. The set of points examined is still every point that can beat
+// the bound, so the result is the same exact argmin.
+__device__ __forceinline__ void nn_thread(const Index &ix, NNLane &q, int start_leaf = -1) {
     int stk[kStack];
     float stkd[kStack];
     int sp = 0;
     int node = 1;
+    if (start_leaf >= 0) {
+        int sib[kStack];
+        int ns = 0;
+        for (int a = ix.L + start_leaf; a > 1; a >>= 1) sib[ns++] = a ^ 1;
+        for (int k = ns - 1; k >= 0; --k) {
+            const int c = sib[k];
+            const float d = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q.xh, q.xl);
+            if (d * kShrink <= q.bestf) {
+                stk[sp] = c;
+                stkd[sp] = d;
+                ++sp;
+            }
+        }
+        node = ix.L + start_leaf;
+    }
     for (;;) {
         if (node < ix.L) {
             const float4 *b = ix.nodes + 4 * node;
@@ -247,6 +347,142 @@ __device__ __forceinline__ void nn_thread(const Index &ix, NNLane &q) {
 }
 
 // ---------------------------------------------------------------------------
+// One query searched by a whole warp (all lanes hold the same query). The
+// search starts at a bucket: the warm-start candidate's, or for a cold query
+// the bucket reached by descending to the nearer child at every level. The
+// siblings of that bucket's path to the root are tested in parallel (one per
+// lane) and pushed on a warp-shared stack, deepest on top, with the bucket
+// itself on top of them. Each round the lanes pop up to 32 nodes:
+//   - an internal node pushes its children that pass the bound (two ballots
+//     compact the pushes: farther children below nearer ones);
+//   - the points of the popped buckets are spread over the lanes, two buckets
+//     per pass of 16 lanes each;
+// and the lexicographic (FP64 d^2, original index) minimum is then reduced
+// across the warp so every lane carries the same bound. Every point that can
+// beat the bound is examined, so the result is the same exact argmin as a
+// serial depth-first search.
+// ---------------------------------------------------------------------------
+constexpr int kWarpStack = 1024;  // per warp; a round grows the stack by <= 96
+
+__device__ __forceinline__ void warp_best(NNLane &q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, q.best_hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, q.best_lo, o);
+        const int oo = __shfl_xor_sync(0xffffffffu, q.best_orig, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, q.best_j, o);
+        const float of = __shfl_xor_sync(0xffffffffu, q.bestf, o);
+        if (lex_less(oh, ol, oo, q.best_hi, q.best_lo, q.best_orig)) {
+            q.best_hi = oh;
+            q.best_lo = ol;
+            q.best_orig = oo;
+            q.best_j = oj;
+        }
+        q.bestf = fminf(q.bestf, of);
+    }
+}
+
+// Returns false if the stack would overflow (the caller flags it as an error).
+__device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, int start_leaf) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int depth = 0;
+    while ((1 << depth) < ix.L) ++depth;
+    if (start_leaf < 0) {   // cold: greedy descent (uniform: every lane computes the same)
+        int node = 1;
+        while (node < ix.L) {
+            const float4 *b = ix.nodes + 4 * node;
+            const float d0 = box_d2(__ldg(b), __ldg(b + 1), q.xh, q.xl);
+            const float d1 = box_d2(__ldg(b + 2), __ldg(b + 3), q.xh, q.xl);
+            node = 2 * node + (d1 < d0 ? 1 : 0);
+        }
+        start_leaf = node - ix.L;
+    }
+    int sp;
+    {
+        int c = 0;
+        bool pass = false;
+        if (lane < depth) {   // the sibling of the path node at level lane + 1
+            c = ((ix.L + start_leaf) >> (depth - 1 - lane)) ^ 1;
+            pass = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q.xh, q.xl) * kShrink <= q.bestf;
+        }
+        const unsigned m = __ballot_sync(FULL, pass);
+        if (pass) stk[__popc(m & below)] = c;
+        sp = __popc(m);
+        if (lane == 0) stk[sp] = ix.L + start_leaf;
+        ++sp;
+    }
+    __syncwarp();
+    const int leaf_parent_level = depth - 1;   // nodes at this level have bucket children
+    while (sp > 0) {
+        const int k = min(32, sp);
+        const int node = (lane < k) ? stk[sp - 1 - lane] : 0;
+        sp -= k;
+        __syncwarp();
+        // An internal node two or more levels above the buckets is expanded to
+        // its four grandchildren (boxes in two adjacent 64-byte lines), a node
+        // just above the buckets to its two children: two levels per round.
+        int c[4] = {0, 0, 0, 0};
+        bool ok[4] = {false, false, false, false};
+        bool leaf_ok = false;
+        if (node != 0) {
+            if (node < ix.L) {
+                const int level = 31 - __clz(node);
+                if (level < leaf_parent_level) {
+                    const float4 *b = ix.nodes + 8 * node;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        c[g] = 4 * node + g;
+                        ok[g] = box_d2(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q.xh, q.xl) * kShrink <= q.bestf;
+                    }
+                } else {
+                    const float4 *b = ix.nodes + 4 * node;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        c[g] = 2 * node + g;
+                        ok[g] = box_d2(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q.xh, q.xl) * kShrink <= q.bestf;
+                    }
+                }
+            } else {
+                leaf_ok = box_d2(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), q.xh, q.xl) * kShrink
+                          <= q.bestf;
+            }
+        }
+        int base = sp;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const unsigned mg = __ballot_sync(FULL, ok[g]);
+            if (base + __popc(mg) > kWarpStack) return false;
+            if (ok[g]) stk[base + __popc(mg & below)] = c[g];
+            base += __popc(mg);
+        }
+        sp = base;
+        unsigned lm = __ballot_sync(FULL, leaf_ok);
+        bool changed = false;
+        while (lm) {   // two buckets per pass: lanes 0-15 and 16-31
+            const int la = __ffs(lm) - 1;
+            lm &= lm - 1u;
+            int lb = la;
+            bool two = false;
+            if (lm) {
+                lb = __ffs(lm) - 1;
+                lm &= lm - 1u;
+                two = true;
+            }
+            const int na = __shfl_sync(FULL, node, la), nb = __shfl_sync(FULL, node, lb);
+            if (lane < 16 || two) {
+                const int j = ((lane < 16 ? na : nb) - ix.L) * kLeaf + (lane & 15);
+                if (j < ix.n) changed |= nn_offer(q, __ldg(ix.pts + j), j);
+            }
+        }
+        if (__ballot_sync(FULL, changed)) warp_best(q);   // only when some lane's bound moved
+        __syncwarp();
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (index.cu, step.cu). All return cudaError_t.
 // ---------------------------------------------------------------------------
 struct TargetDev {
@@ -261,7 +497,10 @@ struct TargetDev {
     // nu_min statistics in caller units (median over q of the median 6-NN distance,
     // resp. plane distance); < 0 until computed.
     double E_Q, H_Q;
+    float near_r2;   // (2 x median bucket-box diagonal)^2
 };
+
+inline Index make_index(const TargetDev &t) { return Index{t.pts, t.nrm, t.nodes, (int)t.n, t.L, t.near_r2}; }
 
 // Per-thread accounting behind fricp_counters (defined in api.cu).
 struct Counters {

@@ -1,13 +1,14 @@
-// The fused step kernel: one correspondence pass of Alg. 1 / Alg. 2 plus the
-// decision that follows it, in a single launch.
-//
-// Each block owns one tile of kBlock sorted source points. Per point (one per
-// thread): transform in FP64 (Sec. 3, x = R p + t), exact closest target point
-// (Eq. 3), residual, Welsch weight and energy term (Eq. 10, Eq. 12, Eq. 16), and
-// that point's contribution to the alignment sums. The block reduces its tile
-// into one FP64 record (fixed shuffle tree, no atomics). The last block to
-// finish reduces all tile records in a fixed order and runs solver_step() on one
-// thread, so the iteration never leaves the device.
+// One device step = one correspondence pass of Alg. 1 / Alg. 2 plus the
+// decision that follows it, in two kernels:
+//   k_nn     FP64 transform (Sec. 3, x = R p + t), warm start from the previous
+//            correspondence, exact closest target point (Eq. 3), one warp per
+//            query (warp_nn);
+//   k_accum  residual, Welsch weight and energy term (Eq. 10, Eq. 12,
+//                Eq. 16) and each point's share of the alignment sums; each block
+//                reduces its tile into one FP64 record (fixed shuffle tree, no
+//                atomics); the last block reduces all records in a fixed order
+//                and runs solver_step() on one thread, so the iteration never
+//                leaves the device.
 #include "fricp_internal.cuh"
 #include "select.cuh"
 #include "solver.cuh"
@@ -51,84 +52,123 @@ __device__ __forceinline__ void reduce_tiles(const double *partial, int ntiles, 
     __syncthreads();
 }
 
+// Step state every kernel of a step reads first (thread 0 loads, block shares).
+struct StepHead {
+    double R[9], t[3], c[3];
+    double scale, inv2nu2;
+    float Rh[9], Rl[9], th[3], tl[3];   // float splits of R and t for the search
+    float cut2;
+    int phase, done, welsch, M;
+};
+
+__device__ __forceinline__ void load_head(const PairState *st, StepHead &h) {
+    h.done = st->done;
+    h.phase = st->phase;
+    h.welsch = st->variant != FRICP_P2P_AA;
+    h.M = st->M;
+    for (int i = 0; i < 9; ++i) h.R[i] = st->Re[i];
+    for (int r = 0; r < 3; ++r) {
+        h.t[r] = st->te[r];
+        h.c[r] = st->c[r];
+    }
+    h.scale = st->s;
+    h.inv2nu2 = st->nu > 0.0 ? 1.0 / (2.0 * st->nu * st->nu) : 0.0;
+    for (int i = 0; i < 9; ++i) split_double(h.R[i], h.Rh[i], h.Rl[i]);
+    for (int r = 0; r < 3; ++r) split_double(h.t[r], h.th[r], h.tl[r]);
+    // Welsch cap radius in caller units: (d_n / s)^2 with d_n^2 / (2 nu^2) = kWelschCut
+    const double cut2 = st->nu > 0.0 ? kWelschCut * 2.0 * st->nu * st->nu / (st->s * st->s) : 0.0;
+    h.cut2 = (cut2 > 0.0 && cut2 < 3.0e38) ? (float)(cut2 * (1.0 + 1e-5)) : __int_as_float(0x7f800000);
+}
+
+__device__ __forceinline__ void transform_point(const StepHead &h, float4 p, double x[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        x[r] = fma(h.R[3 * r], (double)p.x, fma(h.R[3 * r + 1], (double)p.y, fma(h.R[3 * r + 2], (double)p.z, h.t[r])));
+}
+
+// Start a query: FP64 transform, warm start from the previous correspondence,
+// and (Welsch point-to-point, after the nu_max pass) the exact weight cap.
 template <int VAR>
-__global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
+__device__ __forceinline__ void start_query(const StepArgs &a, const StepHead &h, int i, NNLane &q, bool &cold) {
+    float xh[3], xl[3];
+    df_transform(h.Rh, h.Rl, h.th, h.tl, __ldg(a.src + i), xh, xl);
+    nn_init(q, xh, xl);
+    const int j0 = a.prev[i];
+    cold = j0 < 0;
+    if (!cold) nn_seed(q, __ldg(a.ix.pts + j0), j0);
+    // Welsch point-to-point: a point farther than the cap has weight exp(-a) = 0.0
+    // and psi = 1.0 exactly for every candidate that far, so the search radius is
+    // capped there (the sums are bit-identical).
+    if (VAR == 0 && h.welsch && h.phase != PH_INIT && h.cut2 < q.bestf) {
+        q.bestf = h.cut2;
+        cold = false;
+    }
+}
+
+// Search kernel: persistent warps walk the Morton-ordered queries; each query
+// is searched by a whole warp (warp_nn). Writes prev[i] = this pass's
+// correspondence (the next pass's warm start).
+template <int VAR>
+__global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
+    __shared__ StepHead h;
+    __shared__ int s_stk[kBlock / 32][kWarpStack];
+    if (threadIdx.x == 0) load_head(a.st, h);
+    __syncthreads();
+    if (h.done) return;
+    const int lane = threadIdx.x & 31;
+    const int wpb = kBlock / 32;
+    int *stk = s_stk[threadIdx.x >> 5];
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < h.M; i += gridDim.x * wpb) {
+        NNLane q;   // every lane sets up the same query (float arithmetic, broadcast loads)
+        bool cold;
+        start_query<VAR>(a, h, i, q, cold);
+        if (!warp_nn(a.ix, q, stk, q.best_j >= 0 ? q.best_j / kLeaf : -1)) {
+            if (lane == 0) a.st->status = FRICP_ECUDA;   // stack overflow: never expected
+            q.best_j = 0;
+        }
+        if (lane == 0) a.prev[i] = q.best_j < 0 ? 0 : q.best_j;   // -1 only if nothing lies inside the cap
+        __syncwarp();
+    }
+}
+
+// Kernel C: per-point FP64 terms at this pass's correspondences, tile records,
+// and in the last block the fixed-order reduction and the solver step.
+template <int VAR>
+__global__ void __launch_bounds__(kBlock) k_accum(StepArgs a) {
     constexpr int K = VAR ? kSumsP2PL : kSumsP2P;
     PairState *st = a.st;
-    __shared__ double sR[9], sT[3], sC[3], sS[K];
-    __shared__ double s_scale, s_inv2nu2;
-    __shared__ float s_cut2;
-    __shared__ int s_phase, s_done, s_welsch, s_M, s_last;
-    if (threadIdx.x == 0) {
-        s_done = st->done;
-        s_phase = st->phase;
-        s_welsch = st->variant != FRICP_P2P_AA;
-        s_M = st->M;
-        for (int i = 0; i < 9; ++i) sR[i] = st->Re[i];
-        for (int r = 0; r < 3; ++r) {
-            sT[r] = st->te[r];
-            sC[r] = st->c[r];
-        }
-        s_scale = st->s;
-        s_inv2nu2 = st->nu > 0.0 ? 1.0 / (2.0 * st->nu * st->nu) : 0.0;
-        // cap radius in caller units: (d_n / s)^2 with d_n^2 / (2 nu^2) = kWelschCut
-        const double cut2 = st->nu > 0.0 ? kWelschCut * 2.0 * st->nu * st->nu / (st->s * st->s) : 0.0;
-        s_cut2 = (cut2 > 0.0 && cut2 < 3.0e38) ? (float)(cut2 * (1.0 + 1e-5)) : __int_as_float(0x7f800000);
-    }
+    __shared__ StepHead h;
+    __shared__ double sS[K];
+    __shared__ int s_last;
+    if (threadIdx.x == 0) load_head(st, h);
     __syncthreads();
-    if (s_done) return;
-
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    const bool active = i < s_M;
-    float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    double x[3] = {0.0, 0.0, 0.0};
-    NNLane nq;
-    if (active) {
-        p = __ldg(a.src + i);
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-            x[r] = fma(sR[3 * r], (double)p.x, fma(sR[3 * r + 1], (double)p.y, fma(sR[3 * r + 2], (double)p.z, sT[r])));
-        nn_init(nq, x);
-        const int j0 = a.prev[i];
-        if (j0 >= 0) {   // warm start from the previous pass's correspondence
-            const float4 q0 = __ldg(a.ix.pts + j0);
-            nq.bestf = cand_d2f(nq, q0);
-            nq.best64 = cand_d2_64(nq, q0);
-            nq.best_j = j0;
-            nq.best_orig = __float_as_int(q0.w);
-        }
-        // Welsch point-to-point: a point farther than the cap has weight
-        // exp(-a) = 0.0 and psi = 1.0 exactly for every candidate that far, so
-        // the search radius is capped there (the sums are bit-identical).
-        if (VAR == 0 && s_welsch && s_phase != PH_INIT && s_cut2 < nq.bestf) nq.bestf = s_cut2;
-        nn_thread(a.ix, nq);
-        if (nq.best_j < 0) {   // nothing within the cap: any target point is equivalent
-            nq.best_j = 0;
-        }
-    }
+    if (h.done) return;
 
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    if (active) {
-        const int j = nq.best_j;
-        a.prev[i] = j;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i < h.M) {
+        const float4 p = __ldg(a.src + i);
+        double x[3];
+        transform_point(h, p, x);
+        const int j = a.prev[i];
         const float4 q = __ldg(a.ix.pts + j);
         const double dx = x[0] - (double)q.x, dy = x[1] - (double)q.y, dz = x[2] - (double)q.z;
-        const double s = s_scale;
-        const double pt[3] = {(double)p.x - sC[0], (double)p.y - sC[1], (double)p.z - sC[2]};
+        const double s = h.scale;
+        const double pt[3] = {(double)p.x - h.c[0], (double)p.y - h.c[1], (double)p.z - h.c[2]};
         if (VAR == 0) {
             const double d2n = s * s * (dx * dx + dy * dy + dz * dz);
             double w, psi;
-            if (s_welsch) {
-                w = exp(-d2n * s_inv2nu2);
+            if (h.welsch) {
+                w = exp(-d2n * h.inv2nu2);
                 psi = 1.0 - w;
             } else {
                 w = 1.0;
                 psi = d2n;
             }
-            if (s_phase == PH_INIT) a.resid[i] = sqrt(d2n);
-            const double qt[3] = {(double)q.x - sC[0], (double)q.y - sC[1], (double)q.z - sC[2]};
+            if (h.phase == PH_INIT) a.resid[i] = sqrt(d2n);
+            const double qt[3] = {(double)q.x - h.c[0], (double)q.y - h.c[1], (double)q.z - h.c[2]};
             acc[0] = w;
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
@@ -143,13 +183,13 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
         } else {
             const float4 nv = __ldg(a.ix.nrm + j);
             const double n0 = nv.x, n1 = nv.y, n2 = nv.z;
-            const double h = s * (dx * n0 + dy * n1 + dz * n2);
-            if (s_phase == PH_INIT) a.resid[i] = fabs(h);
-            const double g = exp(-h * h * s_inv2nu2);
+            const double hh = s * (dx * n0 + dy * n1 + dz * n2);
+            if (h.phase == PH_INIT) a.resid[i] = fabs(hh);
+            const double g = exp(-hh * hh * h.inv2nu2);
             // y = R p~ in normalised units; z = [y x n; n]
             double y[3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) y[r] = s * (sR[3 * r] * pt[0] + sR[3 * r + 1] * pt[1] + sR[3 * r + 2] * pt[2]);
+            for (int r = 0; r < 3; ++r) y[r] = s * (h.R[3 * r] * pt[0] + h.R[3 * r + 1] * pt[1] + h.R[3 * r + 2] * pt[2]);
             const double z[6] = {y[1] * n2 - y[2] * n1, y[2] * n0 - y[0] * n2, y[0] * n1 - y[1] * n0, n0, n1, n2};
             int t = 0;
 #pragma unroll
@@ -157,7 +197,7 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
                 const double gz = g * z[r];
 #pragma unroll
                 for (int c = r; c < 6; ++c) acc[t++] = gz * z[c];
-                acc[21 + r] = gz * h;
+                acc[21 + r] = gz * hh;
             }
             acc[27] = 1.0 - g;
         }
@@ -170,8 +210,8 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
     if (!s_last) return;
     __threadfence();
     reduce_tiles<K>(a.partial, gridDim.x, sS);
-    if (s_phase == PH_INIT) {
-        const int n = s_M;
+    if (h.phase == PH_INIT) {
+        const int n = h.M;
         const double lo = block_kth(a.resid, n, (n - 1) / 2);
         const double hi = (n % 2) ? lo : block_kth(a.resid, n, n / 2);
         if (threadIdx.x == 0) {
@@ -191,18 +231,22 @@ __global__ void __launch_bounds__(128) k_closest(Index ix, const float *__restri
                                                  double *__restrict__ d2) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < m;
-    double x[3] = {0.0, 0.0, 0.0};
-    NNLane q;
     if (active) {
-        const double p0 = p[3 * i], p1 = p[3 * i + 1], p2 = p[3 * i + 2];
-        for (int r = 0; r < 3; ++r) x[r] = fma(T[3 * r], p0, fma(T[3 * r + 1], p1, fma(T[3 * r + 2], p2, T[9 + r])));
-        nn_init(q, x);
+        float Rh[9], Rl[9], th[3], tl[3], xh[3], xl[3];
+        for (int k = 0; k < 9; ++k) split_double(T[k], Rh[k], Rl[k]);
+        for (int r = 0; r < 3; ++r) split_double(T[9 + r], th[r], tl[r]);
+        const float4 pp = make_float4(p[3 * i], p[3 * i + 1], p[3 * i + 2], 0.0f);
+        df_transform(Rh, Rl, th, tl, pp, xh, xl);
+        NNLane q;
+        nn_init(q, xh, xl);
         nn_thread(ix, q);
         if (q.best_j < 0) q.best_j = 0;   // only for a non-finite x
-    }
-    if (active) {
-        idx[i] = __float_as_int(__ldg(ix.pts + q.best_j).w);
-        d2[i] = q.best64;
+        const float4 qq = __ldg(ix.pts + q.best_j);
+        double x[3];
+        for (int r = 0; r < 3; ++r) x[r] = fma(T[3 * r], (double)pp.x, fma(T[3 * r + 1], (double)pp.y, fma(T[3 * r + 2], (double)pp.z, T[9 + r])));
+        const double dx = x[0] - (double)qq.x, dy = x[1] - (double)qq.y, dz = x[2] - (double)qq.z;
+        idx[i] = __float_as_int(qq.w);
+        d2[i] = dx * dx + dy * dy + dz * dz;
     }
 }
 
@@ -223,12 +267,30 @@ __global__ void k_setup_eval(PairState *st, const double *T) {
 
 }  // namespace
 
+// Blocks of the search kernel (persistent warps): enough to fill every SM.
+int nn_blocks(int M) {
+    static int nb = 0;
+    if (nb == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nn<0>, kBlock, 0);
+        nb = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+    }
+    const int need = (M + kBlock / 32 - 1) / (kBlock / 32);
+    return need < nb ? need : nb;
+}
+
 cudaError_t launch_step(const StepArgs &a, int variant, int ntiles, cudaStream_t s) {
-    if (variant == FRICP_P2PL_WELSCH_AA)
-        k_step<1><<<ntiles, kBlock, 0, s>>>(a);
-    else
-        k_step<0><<<ntiles, kBlock, 0, s>>>(a);
-    counters().launches += 1;
+    const int nb = nn_blocks(ntiles * kBlock);
+    if (variant == FRICP_P2PL_WELSCH_AA) {
+        k_nn<1><<<nb, kBlock, 0, s>>>(a);
+        k_accum<1><<<ntiles, kBlock, 0, s>>>(a);
+    } else {
+        k_nn<0><<<nb, kBlock, 0, s>>>(a);
+        k_accum<0><<<ntiles, kBlock, 0, s>>>(a);
+    }
+    counters().launches += 2;
     return cudaGetLastError();
 }
 
@@ -240,7 +302,7 @@ cudaError_t launch_closest(const TargetDev *t, const float *p_dev, int64_t m, co
     e = cudaMemcpyAsync(dT, T, 12 * sizeof(double), cudaMemcpyHostToDevice, s);
     counters().h2d += 12 * sizeof(double);
     if (e == cudaSuccess) {
-        Index ix{t->pts, t->nrm, t->nodes, (int)t->n, t->L};
+        const Index ix = make_index(*t);
         k_closest<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(ix, p_dev, m, dT, idx, d2);
         counters().launches += 1;
         e = cudaGetLastError();
