@@ -156,88 +156,136 @@ FRICP_HD inline void se3_log(const double T[12], double xi[6]) {
 }
 
 // Rotation of the weighted Procrustes problem (Eq. 4 / Eq. 12, "closed form via
-// SVD"): for H = sum w (p - pbar)(q - qbar)^T = U S V^T, R = V diag(1,1,d) U^T with
-// d = sign det(V U^T) applied to the smallest singular value. The SVD is a
-// one-sided (Hestenes) Jacobi iteration on the columns of H; the singular vector
-// of the smallest singular value is completed by a cross product so a rank-2 H
-// (planar data) keeps a unique answer. Returns false when rank(H) < 2.
+// SVD"): R maximises tr(R H) over SO(3) for H = sum w (p - pbar)(q - qbar)^T,
+// i.e. R = V diag(1,1,d) U^T with H = U S V^T and d = sign det(V U^T).
+//
+// Computed in three parts, since dependent FP64 operations are slow on this GPU:
+//   1. a one-sided (Hestenes) Jacobi SVD of H / max|H| in float; the singular
+//      vector of the smallest singular value is completed by a cross product,
+//      so a rank-2 H (planar data) keeps a unique answer; R0 = V diag(1,1,d) U^T;
+//   2. two Newton-Schulz steps R <- R (3 I - R^T R) / 2 in FP64 make R0
+//      orthogonal to FP64 precision;
+//   3. two Newton steps on SO(3) in FP64: with A = R H, g = vee(A - A^T) and
+//      K = tr(A) I - (A + A^T) / 2 (positive definite near the maximiser),
+//      w = K^-1 g and R <- exp(w^) R. Each step squares the float error, so
+//      R is the FP64 maximiser (the same one the FP64 SVD gives).
+// Returns false when rank(H) < 2 or the Newton system is not positive definite.
 FRICP_HD inline bool procrustes_rotation(const double H[9], double R[9]) {
-    double A[9], V[9];
+    double hmax = 0.0;
+    for (int i = 0; i < 9; ++i) hmax = fmax(hmax, fabs(H[i]));
+    if (!(hmax > 0.0) || !isfinite(hmax)) return false;
+    const double ihm = rcp64(hmax);
+    float A[9], V[9];
     for (int i = 0; i < 9; ++i) {
-        A[i] = H[i];
-        V[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        A[i] = (float)(H[i] * ihm);
+        V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
     }
     const int P_[3] = {0, 0, 1}, Q_[3] = {1, 2, 2};
-    for (int sweep = 0; sweep < 20; ++sweep) {
-        double off = 0.0;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        float off = 0.0f;
         for (int pr = 0; pr < 3; ++pr) {
             const int p = P_[pr], q = Q_[pr];
-            double al = 0.0, be = 0.0, ga = 0.0;
+            float al = 0.0f, be = 0.0f, ga = 0.0f;
             for (int r = 0; r < 3; ++r) {
-                al += A[3 * r + p] * A[3 * r + p];
-                be += A[3 * r + q] * A[3 * r + q];
-                ga += A[3 * r + p] * A[3 * r + q];
+                al = fmaf(A[3 * r + p], A[3 * r + p], al);
+                be = fmaf(A[3 * r + q], A[3 * r + q], be);
+                ga = fmaf(A[3 * r + p], A[3 * r + q], ga);
             }
-            if (ga == 0.0) continue;
-            const double rel = fabs(ga) * rsqrt64(al * be);
-            off = fmax(off, rel);
-            if (!(rel > 1e-16)) continue;
-            // Rotation angle in float (any angle near the exact one makes the same
-            // progress; the fixed point is the exact SVD), then (cs, sn) made unit
-            // length in FP64 so V stays orthogonal to FP64 precision.
-            const float zf = (float)(be - al) / (2.0f * (float)ga);
-            const float tf = copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(1.0f + zf * zf));
-            const float cf = 1.0f / sqrtf(1.0f + tf * tf);
-            double cs = (double)cf, sn = (double)(cf * tf);
-            for (int it = 0; it < 2; ++it) {
-                const double nn = cs * cs + sn * sn;
-                const double corr = 1.5 - 0.5 * nn;
-                cs *= corr;
-                sn *= corr;
-            }
+            if (ga == 0.0f) continue;
+            const float rel = fabsf(ga) / sqrtf(al * be);
+            off = fmaxf(off, rel);
+            if (!(rel > 1e-8f)) continue;
+            const float zeta = (be - al) / (2.0f * ga);
+            const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+            const float cs = 1.0f / sqrtf(1.0f + t * t), sn = cs * t;
             for (int r = 0; r < 3; ++r) {
-                const double ap = A[3 * r + p], aq = A[3 * r + q];
+                const float ap = A[3 * r + p], aq = A[3 * r + q];
                 A[3 * r + p] = cs * ap - sn * aq;
                 A[3 * r + q] = sn * ap + cs * aq;
-                const double vp = V[3 * r + p], vq = V[3 * r + q];
+                const float vp = V[3 * r + p], vq = V[3 * r + q];
                 V[3 * r + p] = cs * vp - sn * vq;
                 V[3 * r + q] = sn * vp + cs * vq;
             }
         }
-        if (off <= 1e-15) break;
+        if (off <= 1e-7f) break;
     }
-    double sg[3];
-    for (int j = 0; j < 3; ++j)
-        sg[j] = sqrt(A[j] * A[j] + A[3 + j] * A[3 + j] + A[6 + j] * A[6 + j]);
+    float sg[3];
+    for (int j = 0; j < 3; ++j) sg[j] = sqrtf(A[j] * A[j] + A[3 + j] * A[3 + j] + A[6 + j] * A[6 + j]);
     int kmin = 0;
     if (sg[1] < sg[kmin]) kmin = 1;
     if (sg[2] < sg[kmin]) kmin = 2;
     const int a = (kmin == 0) ? 1 : 0;
     const int b = (kmin == 2) ? 1 : 2;
-    const double smax = fmax(sg[a], sg[b]), smid = fmin(sg[a], sg[b]);
-    if (!(smid > 1e-14 * smax) || !(smax > 0.0) || !isfinite(smax)) return false;
-    double U[9];
-    double ua[3], ub[3], uk[3];
-    const double ia = rcp64(sg[a]), ib = rcp64(sg[b]);
+    const float smax = fmaxf(sg[a], sg[b]), smid = fminf(sg[a], sg[b]);
+    if (!(smid > 1e-6f * smax) || !(smax > 0.0f)) return false;
+    float U[9], ua[3], ub[3], uk[3];
     for (int r = 0; r < 3; ++r) {
-        ua[r] = A[3 * r + a] * ia;
-        ub[r] = A[3 * r + b] * ib;
+        ua[r] = A[3 * r + a] / sg[a];
+        ub[r] = A[3 * r + b] / sg[b];
     }
-    cross3(ua, ub, uk);
-    const double nk = rsqrt64(uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
+    uk[0] = ua[1] * ub[2] - ua[2] * ub[1];
+    uk[1] = ua[2] * ub[0] - ua[0] * ub[2];
+    uk[2] = ua[0] * ub[1] - ua[1] * ub[0];
+    const float nk = 1.0f / sqrtf(uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
     for (int r = 0; r < 3; ++r) {
         U[3 * r + a] = ua[r];
         U[3 * r + b] = ub[r];
         U[3 * r + kmin] = uk[r] * nk;
     }
-    const double d = (det33(V) * det33(U)) < 0.0 ? -1.0 : 1.0;
+    const float detV = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
+                       V[2] * (V[3] * V[7] - V[4] * V[6]);
+    const float detU = U[0] * (U[4] * U[8] - U[5] * U[7]) - U[1] * (U[3] * U[8] - U[5] * U[6]) +
+                       U[2] * (U[3] * U[7] - U[4] * U[6]);
+    const float d = (detV * detU) < 0.0f ? -1.0f : 1.0f;
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) {
-            double acc = 0.0;
-            for (int j = 0; j < 3; ++j) acc += V[3 * r + j] * (j == kmin ? d : 1.0) * U[3 * c + j];
-            R[3 * r + c] = acc;
+            float acc = 0.0f;
+            for (int j = 0; j < 3; ++j) acc += V[3 * r + j] * (j == kmin ? d : 1.0f) * U[3 * c + j];
+            R[3 * r + c] = (double)acc;
         }
+    // Newton-Schulz: orthogonal to FP64 precision
+    for (int it = 0; it < 2; ++it) {
+        double RtR[9], T[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                RtR[3 * r + c] = R[r] * R[c] + R[3 + r] * R[3 + c] + R[6 + r] * R[6 + c];
+        for (int i = 0; i < 9; ++i) RtR[i] = ((i % 4 == 0) ? 1.5 : 0.0) - 0.5 * RtR[i];
+        mul33(R, RtR, T);
+        for (int i = 0; i < 9; ++i) R[i] = T[i];
+    }
+    // Newton on SO(3): R <- exp(w^) R with (tr(A) I - sym(A)) w = vee(A - A^T), A = R H
+    for (int it = 0; it < 2; ++it) {
+        double Am[9];
+        mul33(R, H, Am);
+        const double g[3] = {Am[5] - Am[7], Am[6] - Am[2], Am[1] - Am[3]};
+        const double tr = Am[0] + Am[4] + Am[8];
+        const double k00 = tr - Am[0], k11 = tr - Am[4], k22 = tr - Am[8];
+        const double k01 = -0.5 * (Am[1] + Am[3]), k02 = -0.5 * (Am[2] + Am[6]), k12 = -0.5 * (Am[5] + Am[7]);
+        const double c00 = k11 * k22 - k12 * k12, c01 = k02 * k12 - k01 * k22, c02 = k01 * k12 - k02 * k11;
+        const double c11 = k00 * k22 - k02 * k02, c12 = k01 * k02 - k00 * k12, c22 = k00 * k11 - k01 * k01;
+        const double det = k00 * c00 + k01 * c01 + k02 * c02;
+        if (!(det > 0.0) || !(k00 > 0.0) || !isfinite(det)) return false;
+        const double idet = rcp64(det);
+        const double w[3] = {(c00 * g[0] + c01 * g[1] + c02 * g[2]) * idet,
+                             (c01 * g[0] + c11 * g[1] + c12 * g[2]) * idet,
+                             (c02 * g[0] + c12 * g[1] + c22 * g[2]) * idet};
+        double W[9], W2[9], E[9], T[9], ea, eb, ec;
+        hat3(w, W);
+        mul33(W, W, W2);
+        exp_coeffs(w[0] * w[0] + w[1] * w[1] + w[2] * w[2], &ea, &eb, &ec);
+        for (int i = 0; i < 9; ++i) E[i] = ((i % 4 == 0) ? 1.0 : 0.0) + ea * W[i] + eb * W2[i];
+        mul33(E, R, T);
+        for (int i = 0; i < 9; ++i) R[i] = T[i];
+    }
     return true;
+}
+
+// Six-term dot product as a balanced tree (short dependency chain).
+FRICP_HD inline double dot6(const double a[6], const double b[6]) {
+    const double s01 = fma(a[1], b[1], a[0] * b[0]);
+    const double s23 = fma(a[3], b[3], a[2] * b[2]);
+    const double s45 = fma(a[5], b[5], a[4] * b[4]);
+    return (s01 + s23) + s45;
 }
 
 // Anderson coefficients (Sec. 4.1, Eq. 6): theta = argmin || f - D theta ||_2 for
@@ -246,8 +294,9 @@ FRICP_HD inline bool procrustes_rotation(const double H[9], double R[9]) {
 FRICP_HD inline bool anderson_lstsq(double D[6][kMaxM], double f[6], int mk, double theta[kMaxM]) {
     double Rd[kMaxM];
     for (int j = 0; j < mk; ++j) {
-        double nrm2 = 0.0;
-        for (int i = j; i < 6; ++i) nrm2 += D[i][j] * D[i][j];
+        double col[6];
+        for (int i = 0; i < 6; ++i) col[i] = (i < j) ? 0.0 : D[i][j];
+        const double nrm2 = dot6(col, col);
         const double nrm = nrm2 > 0.0 ? nrm2 * rsqrt64(nrm2) : 0.0;
         const double alpha = -copysign(nrm, D[j][j]);
         Rd[j] = alpha;
@@ -255,19 +304,16 @@ FRICP_HD inline bool anderson_lstsq(double D[6][kMaxM], double f[6], int mk, dou
         double v[6];
         for (int i = 0; i < 6; ++i) v[i] = (i < j) ? 0.0 : D[i][j];
         v[j] -= alpha;
-        double vv = 0.0;
-        for (int i = j; i < 6; ++i) vv += v[i] * v[i];
+        const double vv = dot6(v, v);
         if (vv == 0.0) continue;
         const double ivv2 = 2.0 * rcp64(vv);
         for (int c = j; c < mk; ++c) {
-            double dot = 0.0;
-            for (int i = j; i < 6; ++i) dot += v[i] * D[i][c];
-            const double sc = dot * ivv2;
+            double dc[6];
+            for (int i = 0; i < 6; ++i) dc[i] = D[i][c];
+            const double sc = dot6(v, dc) * ivv2;
             for (int i = j; i < 6; ++i) D[i][c] -= sc * v[i];
         }
-        double dot = 0.0;
-        for (int i = j; i < 6; ++i) dot += v[i] * f[i];
-        const double sc = dot * ivv2;
+        const double sc = dot6(v, f) * ivv2;
         for (int i = j; i < 6; ++i) f[i] -= sc * v[i];
         D[j][j] = alpha;
     }

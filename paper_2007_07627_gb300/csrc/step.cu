@@ -17,24 +17,33 @@ namespace fricp {
 
 namespace {
 
+// Block reduction of K FP64 values per thread through a shared-memory tree
+// (fixed order). A warp-shuffle tree would run every add on all 32 lanes; here
+// each level runs only the adds it needs, which matters with few FP64 units.
+// The upper half of the block folds into the lower half first, so the buffer
+// holds K x kBlock/2 doubles.
 template <int K>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[K], double *out) {
-    __shared__ double sm[kBlock / 32][K];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int H = kBlock / 2;
+    __shared__ double red[K * H];
+    if (threadIdx.x >= H) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sm[wid][k] = v;
+        for (int k = 0; k < K; ++k) red[k * H + threadIdx.x - H] = acc[k];
     }
     __syncthreads();
-    if (threadIdx.x < K) {
-        double v = 0.0;
+    if (threadIdx.x < H) {
 #pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) v += sm[w][threadIdx.x];
-        out[threadIdx.x] = v;
+        for (int k = 0; k < K; ++k) red[k * H + threadIdx.x] += acc[k];
     }
+    __syncthreads();
+    for (int s = H / 2; s > 0; s >>= 1) {
+        for (int e = threadIdx.x; e < K * s; e += kBlock) {
+            const int k = e / s, t = e - k * s;
+            red[k * H + t] += red[k * H + t + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < K) out[threadIdx.x] = red[threadIdx.x * H];
 }
 
 // Fixed-order reduction of the tile records: warp w owns columns w, w+8, ...;
