@@ -95,6 +95,7 @@ typedef struct {
     double  center[3];          /* c, the centroid of Q */
     double  pass_ms;            /* summed device time of step launches when params.time_passes */
     double  wall_ms;            /* host wall time of the call */
+    double  search_ms;          /* part of pass_ms spent in the closest-point search kernel */
 } fricp_result;
 
 typedef struct fricp_target fricp_target;
@@ -132,6 +133,33 @@ fricp_status fricp_register(const fricp_target *target, const float *p_xyz, int6
                             int32_t on_device, const double *T0, const fricp_params *params,
                             void *stream, fricp_result *out, double *trace,
                             int32_t trace_capacity);
+
+/* Batched registration (no counterpart in the paper, which registers one pair
+ * at a time): npairs independent registrations -- pair i registers p_xyz[i]
+ * (m[i] points, host or device per on_device) onto targets[i] with params[i]
+ * (variants may differ) from T0[16*i .. 16*i+15] (T0 == NULL: identity for
+ * all) -- advance together, one device step for all unfinished pairs per set of
+ * launches (plan, search, accumulate/solve), replayed from a CUDA graph of
+ * params[0].steps_per_sync steps. Each pair's result equals, bit for bit, what
+ * fricp_register returns for it alone. The launch shape of the search (queries
+ * per work ticket, blocks per SM) is chosen by timing candidates on the batch's
+ * first pass and remembered per size class (see fricp_batch_last_shape).
+ * Loop controls (use_graph, steps_per_sync, max_steps, timeout_s) come from
+ * params[0]; time_passes is ignored. out: npairs results (wall_ms is the whole
+ * call's). trace: NULL or npairs * trace_capacity doubles, pair i's energies at
+ * trace[i * trace_capacity]. 1 <= npairs <= 4096. Blocks until every result is
+ * on the host. Errors: as fricp_register, with the failing pair named in the
+ * message; per-pair EDEGENERATE is returned in out[i].status. */
+fricp_status fricp_batch_register(int32_t npairs, const fricp_target *const *targets,
+                                  const float *const *p_xyz, const int64_t *m, int32_t on_device,
+                                  const double *T0, const fricp_params *params, void *stream,
+                                  fricp_result *out, double *trace, int32_t trace_capacity);
+
+/* Launch shape the autotuner chose for the last batched or served run on any
+ * thread: queries per search ticket, search blocks per SM, accumulate blocks
+ * per SM. Any pointer may be NULL. Never fails. */
+void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_per_sm,
+                            int32_t *accumulate_blocks_per_sm);
 
 /* The correspondence step alone (Sec. 3, Eq. 3): for every x_i = R p_i + t
  * (T: double[16] row-major, NULL = identity; p_xyz device float32 [m][3]),
@@ -176,7 +204,7 @@ fricp_status fricp_eval_pass(const fricp_target *target, const float *p_xyz, int
  *   - the pass takes the source points in the caller's order (no Morton sort),
  *     so FP64 sums may differ from fricp_eval_pass in the last bits;
  *   - its scratch (solver state, tile records, correspondences, packed points)
- *     is one static device array of about 0.8 MB that every GPU which loads the
+ *     is one static device array of about 0.7 MB that every GPU which loads the
  *     library keeps until the process exits. The call makes no cudaMalloc,
  *     cudaFree or other allocating call.
  * The first call on a device looks up the array's device address (set-up, once

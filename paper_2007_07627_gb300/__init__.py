@@ -55,7 +55,7 @@ class Result(ctypes.Structure):
         ("device_steps", ctypes.c_int32), ("trace_len", ctypes.c_int32), ("pad0", ctypes.c_int32),
         ("nu_max", ctypes.c_double), ("nu_min", ctypes.c_double), ("final_energy", ctypes.c_double),
         ("scale", ctypes.c_double), ("center", ctypes.c_double * 3), ("pass_ms", ctypes.c_double),
-        ("wall_ms", ctypes.c_double),
+        ("wall_ms", ctypes.c_double), ("search_ms", ctypes.c_double),
     ]
 
 
@@ -89,8 +89,13 @@ def lib() -> ctypes.CDLL:
     L.fricp_last_error.restype = ctypes.c_char_p
     L.fricp_last_error.argtypes = []
     L.fricp_version.restype = i32
+    pp = ctypes.POINTER(vp)
+    L.fricp_batch_register.argtypes = [i32, pp, pp, ctypes.POINTER(i64), i32, dp, ctypes.POINTER(Params), vp,
+                                       ctypes.POINTER(Result), dp, i32]
+    L.fricp_batch_last_shape.argtypes = [ctypes.POINTER(i32)] * 3
+    L.fricp_batch_last_shape.restype = None
     for name in ("fricp_params_default", "fricp_target_create", "fricp_target_destroy", "fricp_register",
-                 "fricp_closest_points", "fricp_eval_pass", "fricp_target_nu_min"):
+                 "fricp_closest_points", "fricp_eval_pass", "fricp_target_nu_min", "fricp_batch_register"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -219,6 +224,50 @@ def register(target: Target, p, T0=None, params: Params | None = None, stream=No
     _check(lib().fricp_register(target.handle, pp, m, dev, Tp, ctypes.byref(params), _stream(stream),
                                 ctypes.byref(r), tp, int(trace_capacity)))
     return _result(r, trace if trace_capacity > 0 else None)
+
+
+def batch_register(targets, sources, params=None, T0=None, stream=None, trace_capacity: int = 0) -> list:
+    """fricp_batch_register: every (target, source) pair registered together; one
+    Params per pair (or one for all). Sources are all host arrays or all CUDA
+    tensors. Returns one result dict per pair."""
+    n = len(targets)
+    if len(sources) != n or n == 0:
+        raise ValueError("targets and sources must be non-empty and of equal length")
+    if params is None:
+        params = [params_default()] * n
+    elif isinstance(params, Params):
+        params = [params] * n
+    if len(params) != n:
+        raise ValueError("one Params per pair")
+    pts = [_points(s) for s in sources]
+    devs = {d for _, _, d, _ in pts}
+    if len(devs) != 1:
+        raise ValueError("sources must all be host arrays or all CUDA tensors")
+    tarr = (ctypes.c_void_p * n)(*[t.handle for t in targets])
+    parr = (ctypes.c_void_p * n)(*[p[0] for p in pts])
+    marr = (ctypes.c_int64 * n)(*[p[1] for p in pts])
+    prm = (Params * n)(*params)
+    res = (Result * n)()
+    Ta = None
+    Tp = None
+    if T0 is not None:
+        Ta = np.ascontiguousarray(np.asarray(T0, dtype=np.float64).reshape(n * 16))
+        Tp = Ta.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    trace = np.zeros(n * max(trace_capacity, 0), np.float64)
+    tp = trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace_capacity > 0 else None
+    _check(lib().fricp_batch_register(n, tarr, parr, marr, devs.pop(), Tp, prm, _stream(stream), res, tp,
+                                      int(trace_capacity)))
+    out = []
+    for i in range(n):
+        tr = trace[i * trace_capacity:(i + 1) * trace_capacity] if trace_capacity > 0 else None
+        out.append(_result(res[i], tr))
+    return out
+
+
+def batch_last_shape() -> dict:
+    c, a, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    lib().fricp_batch_last_shape(ctypes.byref(c), ctypes.byref(a), ctypes.byref(b))
+    return {"chunk": c.value, "search_blocks_per_sm": a.value, "accumulate_blocks_per_sm": b.value}
 
 
 def closest_points(target: Target, p, T=None, stream=None):

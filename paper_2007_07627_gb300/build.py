@@ -16,8 +16,8 @@ PKG = pathlib.Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libfricp.so"
-SOURCES = ["api.cu", "index.cu", "step.cu", "static_pass.cu"]
-HEADERS = ["fricp_internal.cuh", "linalg.cuh", "solver.cuh", "select.cuh"]
+SOURCES = ["api.cu", "index.cu", "step.cu", "static_pass.cu", "batch.cu"]
+HEADERS = ["fricp_internal.cuh", "linalg.cuh", "solver.cuh", "select.cuh", "step_common.cuh", "host_common.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -8,9 +8,7 @@
 #include <thread>
 #include <vector>
 
-#include "fricp_internal.cuh"
-#include "linalg.cuh"
-#include "solver.cuh"
+#include "host_common.cuh"
 
 using fricp::PairState;
 using fricp::TargetDev;
@@ -29,167 +27,14 @@ Counters &counters() {
 namespace {
 
 using fricp::counters;
+using namespace fricp::host;
 
 thread_local std::string g_err;
-
-fricp_status fail(fricp_status s, const std::string &msg) {
-    g_err = msg;
-    return s;
-}
-
-fricp_status cuda_fail(cudaError_t e, const char *where) {
-    g_err = std::string(where) + ": " + cudaGetErrorString(e);
-    return FRICP_ECUDA;
-}
-
-// One non-blocking stream per host thread: graphs can be captured on it, and it
-// is ordered after / before the caller's stream with events.
-cudaStream_t work_stream() {
-    thread_local cudaStream_t s = nullptr;
-    if (s == nullptr) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    return s;
-}
-
-struct Ordered {
-    cudaStream_t user, work;
-    cudaEvent_t ev = nullptr;
-    explicit Ordered(void *stream) : user((cudaStream_t)stream), work(work_stream()) {
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        cudaEventRecord(ev, user);
-        cudaStreamWaitEvent(work, ev, 0);
-    }
-    ~Ordered() {
-        cudaEventRecord(ev, work);
-        cudaStreamWaitEvent(user, ev, 0);
-        cudaEventDestroy(ev);
-    }
-};
-
-int *pinned_flag() {
-    thread_local int *p = nullptr;
-    if (p == nullptr) cudaMallocHost(&p, 64);
-    return p;
-}
-
-bool host_finite(const float *x, int64_t n3) {
-    for (int64_t i = 0; i < n3; ++i)
-        if (!std::isfinite(x[i])) return false;
-    return true;
-}
-
-fricp_status check_params(const fricp_params *p) {
-    if (p->variant < FRICP_P2P_AA || p->variant > FRICP_P2PL_WELSCH_AA) return fail(FRICP_EINVAL, "unknown variant");
-    if (p->anderson_m < 0 || p->anderson_m > fricp::kMaxM) return fail(FRICP_EINVAL, "anderson_m must be in 0..5");
-    if (p->max_iters < 1 || p->p2pl_iters_first < 1 || p->p2pl_iters_cap < p->p2pl_iters_first)
-        return fail(FRICP_EINVAL, "iteration caps must be >= 1 and cap >= first");
-    if (p->max_line_search < 0) return fail(FRICP_EINVAL, "max_line_search must be >= 0");
-    if (!(p->eps > 0.0)) return fail(FRICP_EINVAL, "eps must be > 0");
-    if (!(p->nu_min_floor > 0.0)) return fail(FRICP_EINVAL, "nu_min_floor must be > 0");
-    if (p->steps_per_sync < 1 || p->steps_per_sync > 4096) return fail(FRICP_EINVAL, "steps_per_sync in 1..4096");
-    if (p->max_steps < 1) return fail(FRICP_EINVAL, "max_steps must be >= 1");
-    if (!(p->timeout_s > 0.0)) return fail(FRICP_EINVAL, "timeout_s must be > 0");
-    return FRICP_OK;
-}
-
-// Device copy of a caller array (host or device). Frees what it allocated.
-struct DevInput {
-    const float *ptr = nullptr;
-    float *owned = nullptr;
-    cudaStream_t s = nullptr;
-    ~DevInput() {
-        if (owned) cudaFreeAsync(owned, s);
-    }
-};
-
-fricp_status stage_input(const float *x, int64_t n, int on_device, cudaStream_t s, DevInput *out, const char *what) {
-    out->s = s;
-    if (on_device) {
-        out->ptr = x;
-        return FRICP_OK;
-    }
-    if (!host_finite(x, 3 * n)) return fail(FRICP_EINVAL, std::string(what) + " has NaN or Inf");
-    cudaError_t e = cudaMallocAsync(&out->owned, sizeof(float) * 3 * n, s);
-    if (e != cudaSuccess) return fail(FRICP_ENOMEM, std::string("device allocation for ") + what);
-    e = cudaMemcpyAsync(out->owned, x, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "copy input to device");
-    counters().h2d += (int64_t)sizeof(float) * 3 * n;
-    out->ptr = out->owned;
-    return FRICP_OK;
-}
-
-template <class T>
-struct DevBuf {
-    T *p = nullptr;
-    cudaStream_t s = nullptr;
-    bool leak = false;
-    cudaError_t alloc(size_t count, cudaStream_t st) {
-        s = st;
-        return cudaMallocAsync(&p, sizeof(T) * (count > 0 ? count : 1), st);
-    }
-    ~DevBuf() {
-        if (p && !leak) cudaFreeAsync(p, s);
-    }
-};
-
-fricp_status wait_event(cudaEvent_t ev, std::chrono::steady_clock::time_point deadline) {
-    for (;;) {
-        const cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaSuccess) return FRICP_OK;
-        if (e != cudaErrorNotReady) return cuda_fail(e, "waiting for device steps");
-        if (std::chrono::steady_clock::now() > deadline) return fail(FRICP_ETIMEOUT, "registration timed out");
-        std::this_thread::yield();
-    }
-}
-
-// Normalisation of both sets by one similarity x -> s (x - c): c = centroid of Q,
-// s = 1 / diagonal of the bounding box of P u Q (Sec. 6 set-up).
-void normalisation(const TargetDev &t, const float plo[3], const float phi[3], double *s, double c[3]) {
-    double d2 = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        const double lo = std::fmin((double)plo[a], (double)t.lo[a]);
-        const double hi = std::fmax((double)phi[a], (double)t.hi[a]);
-        d2 += (hi - lo) * (hi - lo);
-        c[a] = t.centroid[a];
-    }
-    *s = d2 > 0.0 ? 1.0 / std::sqrt(d2) : 1.0;
-}
-
-void to_normalised(const double *T0, double s, const double c[3], double Tn[12]) {
-    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, t[3] = {0, 0, 0};
-    if (T0) {
-        for (int r = 0; r < 3; ++r) {
-            for (int k = 0; k < 3; ++k) R[3 * r + k] = T0[4 * r + k];
-            t[r] = T0[4 * r + 3];
-        }
-    }
-    for (int i = 0; i < 9; ++i) Tn[i] = R[i];
-    for (int r = 0; r < 3; ++r) {
-        const double Rc = R[3 * r] * c[0] + R[3 * r + 1] * c[1] + R[3 * r + 2] * c[2];
-        Tn[9 + r] = s * (Rc + t[r] - c[r]);
-    }
-}
-
-void to_caller(const double Tn[12], double s, const double c[3], double R[9], double t[3]) {
-    for (int i = 0; i < 9; ++i) R[i] = Tn[i];
-    for (int r = 0; r < 3; ++r) {
-        const double Rc = Tn[3 * r] * c[0] + Tn[3 * r + 1] * c[1] + Tn[3 * r + 2] * c[2];
-        t[r] = Tn[9 + r] / s + c[r] - Rc;
-    }
-}
-
-struct Graph {
-    cudaGraphExec_t exec = nullptr;
-    cudaGraph_t g = nullptr;
-    ~Graph() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (g) cudaGraphDestroy(g);
-    }
-};
 
 // Run fused steps until the state machine is done. Returns the status and the
 // summed device time of the step launches when timing is requested.
 fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const fricp_params &prm, cudaStream_t s,
-                       PairState *st_dev, bool *leak, double *pass_ms) {
+                       PairState *st_dev, bool *leak, double *pass_ms, double *search_ms) {
     using clock = std::chrono::steady_clock;
     const auto deadline = clock::now() + std::chrono::duration_cast<clock::duration>(
                                              std::chrono::duration<double>(prm.timeout_s));
@@ -202,7 +47,7 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
     const bool use_graph = prm.use_graph && !timing;
     std::vector<cudaEvent_t> tev;
     if (timing) {
-        tev.resize(2 * chunk);
+        tev.resize(3 * chunk);
         for (auto &e : tev) cudaEventCreate(&e);
     }
     fricp_status rs = FRICP_OK;
@@ -220,15 +65,16 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
     }
     int64_t steps = 0;
     *pass_ms = 0.0;
+    *search_ms = 0.0;
     while (rs == FRICP_OK) {
         if (use_graph) {
             e = cudaGraphLaunch(graph.exec, s);
             counters().launches += chunk;
         } else {
             for (int k = 0; k < chunk && e == cudaSuccess; ++k) {
-                if (timing) cudaEventRecord(tev[2 * k], s);
-                e = fricp::launch_step(a, variant, ntiles, s);
-                if (timing) cudaEventRecord(tev[2 * k + 1], s);
+                if (timing) cudaEventRecord(tev[3 * k], s);
+                e = fricp::launch_step(a, variant, ntiles, s, timing ? tev[3 * k + 1] : nullptr);
+                if (timing) cudaEventRecord(tev[3 * k + 2], s);
             }
         }
         if (e != cudaSuccess) {
@@ -250,9 +96,11 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
         }
         if (timing) {
             for (int k = 0; k < chunk; ++k) {
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, tev[2 * k], tev[2 * k + 1]);
+                float ms = 0.0f, ms_nn = 0.0f;
+                cudaEventElapsedTime(&ms, tev[3 * k], tev[3 * k + 2]);
+                cudaEventElapsedTime(&ms_nn, tev[3 * k], tev[3 * k + 1]);
                 *pass_ms += ms;
+                *search_ms += ms_nn;
             }
         }
         if (*done_h) break;
@@ -264,30 +112,6 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
     for (auto &ev : tev) cudaEventDestroy(ev);
     cudaEventDestroy(poll);
     return rs;
-}
-
-PairState initial_state(const fricp_params &prm, int64_t m, int ntiles, double s, const double c[3],
-                        double nu_min, int trace_cap) {
-    PairState h;
-    std::memset(&h, 0, sizeof(h));
-    h.variant = prm.variant;
-    h.m = prm.anderson_m;
-    h.max_iters = prm.max_iters;
-    h.cap_first = prm.p2pl_iters_first;
-    h.cap_max = prm.p2pl_iters_cap;
-    h.max_ls = prm.max_line_search;
-    h.M = (int)m;
-    h.ntiles = ntiles;
-    h.trace_cap = trace_cap;
-    h.eps = prm.eps;
-    h.s = s;
-    for (int a = 0; a < 3; ++a) h.c[a] = c[a];
-    h.nu_max_given = prm.nu_max > 0.0;
-    h.nu_max = prm.nu_max > 0.0 ? prm.nu_max : 0.0;
-    h.nu_min = nu_min;
-    h.E_prev = INFINITY;
-    h.cap = prm.p2pl_iters_first;
-    return h;
 }
 
 }  // namespace
@@ -432,9 +256,9 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     DevBuf<float4> src;
     DevBuf<PairState> st_dev;
     DevBuf<double> partial, resid, trace_dev;
-    DevBuf<int> prev, queue;
+    DevBuf<int> prev;
     if (src.alloc(m, s) != cudaSuccess || st_dev.alloc(1, s) != cudaSuccess || prev.alloc(m, s) != cudaSuccess ||
-        queue.alloc(m, s) != cudaSuccess || partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
+        partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
         resid.alloc(robust ? m : 1, s) != cudaSuccess || trace_dev.alloc(trace_capacity, s) != cudaSuccess)
         return fail(FRICP_ENOMEM, "device allocation for the registration");
     float plo[3], phi[3];
@@ -444,36 +268,9 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     if (bad) return fail(FRICP_EINVAL, "p_xyz has NaN or Inf");
 
     double scale, c[3];
-    normalisation(t->d, plo, phi, &scale, c);
-    double nu_min = 1.0;
-    if (robust) {
-        if (prm.nu_min > 0.0) {
-            nu_min = prm.nu_min;
-        } else {
-            e = fricp::target_nu_stats(const_cast<TargetDev *>(&t->d), s);
-            if (e != cudaSuccess) return cuda_fail(e, "nu_min statistics");
-            nu_min = prm.variant == FRICP_P2PL_WELSCH_AA ? scale * t->d.H_Q / 6.0
-                                                         : scale * t->d.E_Q / (3.0 * std::sqrt(3.0));
-        }
-        nu_min = std::fmax(nu_min, prm.nu_min_floor);
-    }
-    PairState h = initial_state(prm, m, ntiles, scale, c, nu_min, trace_capacity);
-    double T0n[12];
-    to_normalised(T0, scale, c, T0n);
-    if (prm.variant == FRICP_P2PL_WELSCH_AA) {
-        fricp::se3_log(T0n, h.xk);
-        fricp::request_eval_xi(&h, h.xk, 1);
-    } else {
-        fricp::copy_n(h.Tk, T0n, 12);
-        fricp::se3_log(h.Tk, h.logTk);
-        fricp::request_eval_T(&h, h.Tk, 1);
-    }
-    if (robust) {
-        h.phase = fricp::PH_INIT;
-    } else {
-        h.phase = fricp::PH_STAGE_START;
-        h.nu = h.nu_max = h.nu_min = 1.0;
-    }
+    PairState h;
+    st = setup_pair(t->d, prm, m, plo, phi, T0, trace_capacity, s, &h, &scale, c);
+    if (st != FRICP_OK) return st;
     e = cudaMemcpyAsync(st_dev.p, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the solver state");
     counters().h2d += sizeof(h);
@@ -485,15 +282,14 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     a.ix = fricp::make_index(t->d);
     a.src = src.p;
     a.prev = prev.p;
-    a.queue = queue.p;
     a.partial = partial.p;
     a.resid = resid.p;
     a.trace = trace_capacity > 0 ? trace_dev.p : nullptr;
     bool leak = false;
-    double pass_ms = 0.0;
-    st = run_steps(a, prm.variant, ntiles, prm, s, st_dev.p, &leak, &pass_ms);
+    double pass_ms = 0.0, search_ms = 0.0;
+    st = run_steps(a, prm.variant, ntiles, prm, s, st_dev.p, &leak, &pass_ms, &search_ms);
     if (leak) {
-        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = queue.leak = true;
+        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = true;
         p.owned = nullptr;
     }
     if (st != FRICP_OK && st != FRICP_ETIMEOUT) return st;
@@ -511,27 +307,9 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     } else {
         return st;
     }
-    double Tn[12];
-    if (prm.variant == FRICP_P2PL_WELSCH_AA)
-        fricp::se3_exp(r.xk, Tn);
-    else
-        fricp::copy_n(Tn, r.Tk, 12);
-    to_caller(Tn, scale, c, out->R, out->t);
-    out->status = r.status;
-    out->iterations = r.iterations;
-    out->corr_passes = r.corr_passes;
-    out->aa_accepted = r.aa_accepted;
-    out->reverts = r.reverts;
-    out->line_search_trials = r.ls_trials;
-    out->stages = r.stages;
-    out->device_steps = r.device_steps;
-    out->trace_len = r.trace_len < trace_capacity ? r.trace_len : trace_capacity;
-    out->nu_max = r.nu_max;
-    out->nu_min = r.nu_min;
-    out->final_energy = r.final_energy;
-    out->scale = scale;
-    for (int a3 = 0; a3 < 3; ++a3) out->center[a3] = c[a3];
+    fill_result(r, prm.variant, scale, c, trace_capacity, out);
     out->pass_ms = pass_ms;
+    out->search_ms = search_ms;
     out->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     return st;
 }
@@ -555,9 +333,9 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     DevBuf<float4> src;
     DevBuf<PairState> st_dev;
     DevBuf<double> partial, Tdev;
-    DevBuf<int> prev, queue;
+    DevBuf<int> prev;
     if (src.alloc(m, s) != cudaSuccess || st_dev.alloc(1, s) != cudaSuccess || prev.alloc(m, s) != cudaSuccess ||
-        queue.alloc(m, s) != cudaSuccess || partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
+        partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
         Tdev.alloc(12, s) != cudaSuccess)
         return fail(FRICP_ENOMEM, "device allocation");
     float plo[3], phi[3];
@@ -584,7 +362,6 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     a.ix = fricp::make_index(t->d);
     a.src = src.p;
     a.prev = prev.p;
-    a.queue = queue.p;
     a.partial = partial.p;
     a.resid = nullptr;
     a.trace = nullptr;

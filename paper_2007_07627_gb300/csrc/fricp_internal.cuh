@@ -44,7 +44,6 @@ struct Index {
     const float4 *nodes;
     int n;
     int L;
-    float near_r2;   // a warm-started query with a smaller bound searches alone (per thread)
 };
 
 enum Phase : int {
@@ -77,8 +76,6 @@ struct PairState {
     double c[3];       // normalisation centre (centroid of Q), caller units
     // ---- machine
     unsigned int counter;   // last-block ticket of the running step
-    unsigned int far_count; // queries queued for the warp-per-query search in this step
-    unsigned int far_next;  // next queued query to hand out
     int phase;
     int done;
     int status;
@@ -116,7 +113,6 @@ struct StepArgs {
     const float4 *src;     // M sorted source points
     int *prev;             // M: correspondence (sorted target index) of the last pass, -1 if none;
                            //    the search kernels overwrite it with this pass's correspondence
-    int *queue;            // M: indices of the queries handed to the warp-per-query search
     double *partial;       // ntiles * kMaxSums
     double *resid;         // M per-point residuals (PH_INIT)
     double *trace;         // trace_cap energies
@@ -497,10 +493,9 @@ struct TargetDev {
     // nu_min statistics in caller units (median over q of the median 6-NN distance,
     // resp. plane distance); < 0 until computed.
     double E_Q, H_Q;
-    float near_r2;   // (2 x median bucket-box diagonal)^2
 };
 
-inline Index make_index(const TargetDev &t) { return Index{t.pts, t.nrm, t.nodes, (int)t.n, t.L, t.near_r2}; }
+inline Index make_index(const TargetDev &t) { return Index{t.pts, t.nrm, t.nodes, (int)t.n, t.L}; }
 
 // Per-thread accounting behind fricp_counters (defined in api.cu).
 struct Counters {
@@ -520,7 +515,9 @@ cudaError_t prepare_source(const float *p_dev, int64_t m, cudaStream_t s, float4
                            float lo[3], float hi[3], int *bad_input);
 cudaError_t launch_closest(const TargetDev *t, const float *p_dev, int64_t m, const double T[12],
                            int64_t *idx, double *d2, cudaStream_t s);
-cudaError_t launch_step(const StepArgs &a, int variant, int ntiles, cudaStream_t s);
+// One device step: the closest-point search kernel, then the accumulate/solve
+// kernel. When `mid` is given it is recorded between the two.
+cudaError_t launch_step(const StepArgs &a, int variant, int ntiles, cudaStream_t s, cudaEvent_t mid = nullptr);
 cudaError_t launch_setup_eval_xi(PairState *st, const double *T_normalized12, cudaStream_t s);
 
 }  // namespace fricp

@@ -424,22 +424,6 @@ cudaError_t build_target(const float *q_dev, const float *n_dev, int64_t n, cuda
     cudaFreeAsync(order, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    // Near threshold: queries whose bound is within two bucket-box diagonals
-    // (median over the buckets) search alone in kernel A.
-    const int64_t nb = (n + kLeaf - 1) / kLeaf;
-    std::vector<float4> leaves(2 * nb);
-    e = cudaMemcpy(leaves.data(), t->nodes + 2 * L, sizeof(float4) * 2 * nb, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return e;
-    counters().d2h += (int64_t)sizeof(float4) * 2 * nb;
-    std::vector<float> diag(nb);
-    for (int64_t l = 0; l < nb; ++l) {
-        const float4 lo = leaves[2 * l], hi = leaves[2 * l + 1];
-        const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
-        diag[l] = std::sqrt(dx * dx + dy * dy + dz * dz);
-    }
-    std::nth_element(diag.begin(), diag.begin() + nb / 2, diag.end());
-    const float r = 2.0f * diag[nb / 2];
-    t->near_r2 = r > 0.0f ? r * r : 1e-30f;
     return cudaSuccess;
 }
 

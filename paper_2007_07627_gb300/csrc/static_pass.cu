@@ -25,16 +25,14 @@ constexpr size_t kStateBytes = 16384;                               // >= sizeof
 constexpr size_t kTBytes = 256;                                     // 12 doubles, padded
 constexpr size_t kPartialBytes = sizeof(double) * kStaticTiles * fricp::kMaxSums;
 constexpr size_t kPrevBytes = sizeof(int) * kStaticMaxPoints;
-constexpr size_t kQueueBytes = sizeof(int) * kStaticMaxPoints;
 constexpr size_t kSrcBytes = sizeof(float4) * kStaticMaxPoints;
 constexpr size_t kOffT = kStateBytes;
 constexpr size_t kOffPartial = kOffT + kTBytes;
 constexpr size_t kOffPrev = kOffPartial + kPartialBytes;
-constexpr size_t kOffQueue = kOffPrev + kPrevBytes;
-constexpr size_t kOffSrc = kOffQueue + kQueueBytes;
-constexpr size_t kScratchBytes = kOffSrc + kSrcBytes;               // about 0.8 MB
+constexpr size_t kOffSrc = kOffPrev + kPrevBytes;
+constexpr size_t kScratchBytes = kOffSrc + kSrcBytes;               // about 0.7 MB
 static_assert(sizeof(PairState) <= kStateBytes, "state region too small");
-static_assert(kOffPartial % 256 == 0 && kOffPrev % 256 == 0 && kOffQueue % 256 == 0 && kOffSrc % 256 == 0,
+static_assert(kOffPartial % 256 == 0 && kOffPrev % 256 == 0 && kOffSrc % 256 == 0,
               "region alignment");
 
 // The scratch of every call. Host code must not pass this name to a kernel: on
@@ -95,7 +93,6 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
     double *T_dev = reinterpret_cast<double *>(base + kOffT);
     double *partial = reinterpret_cast<double *>(base + kOffPartial);
     int *prev = reinterpret_cast<int *>(base + kOffPrev);
-    int *queue = reinterpret_cast<int *>(base + kOffQueue);
     float4 *src = reinterpret_cast<float4 *>(base + kOffSrc);
     const int ntiles = (int)((m + fricp::kBlock - 1) / fricp::kBlock);
 
@@ -123,9 +120,8 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
         T12[9 + r] = T_normalized[4 * r + 3];
     }
     // Every region the pass reads is rewritten here, so nothing from the last
-    // call leaks in: the whole state (its last-block counter and queue counters
-    // included), T, the correspondences (-1: none) and the packed source. Tile
-    // records and queue entries are written by the pass before they are read.
+    // call leaks in: the whole state (its last-block counter included), T, the correspondences (-1: none) and the packed source. Tile
+    // records are written by the pass before they are read.
     cudaError_t e = cudaMemcpyAsync(st_dev, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(T_dev, T12, sizeof(T12), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(prev, 0xff, sizeof(int) * m, s);
@@ -140,7 +136,6 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
     a.ix = fricp::make_index(td);
     a.src = src;
     a.prev = prev;
-    a.queue = queue;
     a.partial = partial;
     a.resid = nullptr;
     a.trace = nullptr;

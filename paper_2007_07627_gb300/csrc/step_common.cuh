@@ -1,0 +1,235 @@
+// Device code shared by the single-registration step (step.cu) and the batched
+// step (batch.cu): the per-step head of a registration, the start of a query,
+// each point's share of the alignment sums, the block and tile reductions and
+// the work of the block that completes a registration's pass. Both paths run
+// exactly this arithmetic in this order, so a registration gives the same bits
+// alone and inside a batch.
+#pragma once
+
+#include "fricp_internal.cuh"
+#include "select.cuh"
+#include "solver.cuh"
+
+namespace fricp {
+namespace {
+
+// Shared buffer of block_reduce_store: K x kBlock/2 doubles.
+constexpr int kRedHalf = kBlock / 2;
+
+// Block reduction of K FP64 values per thread through a shared-memory tree
+// (fixed order). A warp-shuffle tree would run every add on all 32 lanes; here
+// each level runs only the adds it needs, which matters with few FP64 units.
+// The upper half of the block folds into the lower half first. `red` holds
+// K * kRedHalf doubles of shared memory.
+template <int K>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[K], double *out, double *red) {
+    constexpr int H = kRedHalf;
+    if (threadIdx.x >= H) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * H + threadIdx.x - H] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < H) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * H + threadIdx.x] += acc[k];
+    }
+    __syncthreads();
+    for (int s = H / 2; s > 0; s >>= 1) {
+        for (int e = threadIdx.x; e < K * s; e += kBlock) {
+            const int k = e / s, t = e - k * s;
+            red[k * H + t] += red[k * H + t + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < K) out[threadIdx.x] = red[threadIdx.x * H];
+    __syncthreads();   // `red` may be reused right away
+}
+
+// Fixed-order reduction of the tile records: warp w owns columns w, w+8, ...;
+// lane l sums rows l, l+32, ... and a shuffle tree finishes the column.
+template <int K>
+__device__ __forceinline__ void reduce_tiles(const double *partial, int ntiles, double *S) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = wid; k < K; k += kBlock / 32) {
+        double v = 0.0;
+        for (int r = lane; r < ntiles; r += 32) v += __ldcg(partial + (size_t)r * K + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) S[k] = v;
+    }
+    __syncthreads();
+}
+
+// Step state every kernel of a step reads first.
+struct StepHead {
+    double R[9], t[3], c[3];
+    double scale, inv2nu2;
+    float Rh[9], Rl[9], th[3], tl[3];   // float splits of R and t for the search
+    float cut2;
+    int phase, done, welsch, M, variant;
+};
+
+__device__ __forceinline__ void load_head(const PairState *st, StepHead &h) {
+    h.done = st->done;
+    h.phase = st->phase;
+    h.variant = st->variant;
+    h.welsch = st->variant != FRICP_P2P_AA;
+    h.M = st->M;
+    for (int i = 0; i < 9; ++i) h.R[i] = st->Re[i];
+    for (int r = 0; r < 3; ++r) {
+        h.t[r] = st->te[r];
+        h.c[r] = st->c[r];
+    }
+    h.scale = st->s;
+    h.inv2nu2 = st->nu > 0.0 ? 1.0 / (2.0 * st->nu * st->nu) : 0.0;
+    for (int i = 0; i < 9; ++i) split_double(h.R[i], h.Rh[i], h.Rl[i]);
+    for (int r = 0; r < 3; ++r) split_double(h.t[r], h.th[r], h.tl[r]);
+    // Welsch cap radius in caller units: (d_n / s)^2 with d_n^2 / (2 nu^2) = kWelschCut
+    const double cut2 = st->nu > 0.0 ? kWelschCut * 2.0 * st->nu * st->nu / (st->s * st->s) : 0.0;
+    h.cut2 = (cut2 > 0.0 && cut2 < 3.0e38) ? (float)(cut2 * (1.0 + 1e-5)) : __int_as_float(0x7f800000);
+}
+
+__device__ __forceinline__ void transform_point(const StepHead &h, float4 p, double x[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        x[r] = fma(h.R[3 * r], (double)p.x, fma(h.R[3 * r + 1], (double)p.y, fma(h.R[3 * r + 2], (double)p.z, h.t[r])));
+}
+
+// Start a query: double-float transform, warm start from the previous
+// correspondence, and (Welsch point-to-point after the nu_max pass) the exact
+// weight cap: a point farther than the cap has weight exp(-a) = 0.0 and
+// psi = 1.0 exactly for every candidate that far, so the search radius is capped
+// there (the sums are bit-identical).
+__device__ __forceinline__ void start_query(const Index &ix, const float4 *src, const int *prev, const StepHead &h,
+                                            int i, bool p2p, NNLane &q) {
+    float xh[3], xl[3];
+    df_transform(h.Rh, h.Rl, h.th, h.tl, __ldg(src + i), xh, xl);
+    nn_init(q, xh, xl);
+    const int j0 = prev[i];
+    if (j0 >= 0) nn_seed(q, __ldg(ix.pts + j0), j0);
+    if (p2p && h.welsch && h.phase != PH_INIT && h.cut2 < q.bestf) q.bestf = h.cut2;
+}
+
+// One query searched by the whole warp; lane 0 stores the correspondence (the
+// next pass's warm start). Returns false on a search-stack overflow.
+__device__ __forceinline__ bool search_query(const Index &ix, const float4 *src, int *prev, const StepHead &h, int i,
+                                             bool p2p, int *stk) {
+    NNLane q;   // every lane sets up the same query (float arithmetic, broadcast loads)
+    start_query(ix, src, prev, h, i, p2p, q);
+    const bool ok = warp_nn(ix, q, stk, q.best_j >= 0 ? q.best_j / kLeaf : -1);
+    if (!ok) q.best_j = 0;
+    if ((threadIdx.x & 31) == 0) prev[i] = q.best_j < 0 ? 0 : q.best_j;   // -1 only if nothing lies inside the cap
+    __syncwarp();
+    return ok;
+}
+
+// Point i's share of the pass sums at this pass's correspondence (FP64):
+// Welsch weight and energy term (Eq. 10, Eq. 12, Eq. 16); point-to-point: the
+// weighted centroids and cross-covariance terms; point-to-plane: g z z^T, g z h
+// and the energy with z = [y x n; n] (App. D). At PH_INIT the residual is kept
+// for the nu_max median.
+template <int VAR>
+__device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, const float4 *src, const int *prev,
+                                            double *resid, int i, double (&acc)[VAR ? kSumsP2PL : kSumsP2P]) {
+    const float4 p = __ldg(src + i);
+    double x[3];
+    transform_point(h, p, x);
+    const int j = prev[i];
+    const float4 q = __ldg(ix.pts + j);
+    const double dx = x[0] - (double)q.x, dy = x[1] - (double)q.y, dz = x[2] - (double)q.z;
+    const double s = h.scale;
+    const double pt[3] = {(double)p.x - h.c[0], (double)p.y - h.c[1], (double)p.z - h.c[2]};
+    if (VAR == 0) {
+        const double d2n = s * s * (dx * dx + dy * dy + dz * dz);
+        double w, psi;
+        if (h.welsch) {
+            w = exp(-d2n * h.inv2nu2);
+            psi = 1.0 - w;
+        } else {
+            w = 1.0;
+            psi = d2n;
+        }
+        if (h.phase == PH_INIT) resid[i] = sqrt(d2n);
+        const double qt[3] = {(double)q.x - h.c[0], (double)q.y - h.c[1], (double)q.z - h.c[2]};
+        acc[0] = w;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            acc[1 + u] = w * pt[u];
+            acc[4 + u] = w * qt[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+            for (int v = 0; v < 3; ++v) acc[7 + 3 * u + v] = acc[1 + u] * qt[v];
+        acc[16] = psi;
+    } else {
+        const float4 nv = __ldg(ix.nrm + j);
+        const double n0 = nv.x, n1 = nv.y, n2 = nv.z;
+        const double hh = s * (dx * n0 + dy * n1 + dz * n2);
+        if (h.phase == PH_INIT) resid[i] = fabs(hh);
+        const double g = exp(-hh * hh * h.inv2nu2);
+        // y = R p~ in normalised units; z = [y x n; n]
+        double y[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) y[r] = s * (h.R[3 * r] * pt[0] + h.R[3 * r + 1] * pt[1] + h.R[3 * r + 2] * pt[2]);
+        const double z[6] = {y[1] * n2 - y[2] * n1, y[2] * n0 - y[0] * n2, y[0] * n1 - y[1] * n0, n0, n1, n2};
+        int t = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            const double gz = g * z[r];
+#pragma unroll
+            for (int c = r; c < 6; ++c) acc[t++] = gz * z[c];
+            acc[21 + r] = gz * hh;
+        }
+        acc[27] = 1.0 - g;
+    }
+}
+
+// One tile of kBlock points of a registration: per-point terms, then the tile's
+// FP64 record at partial[tile * K]. Returns true in every thread of the block
+// that completed the registration's pass (the last of its tiles to finish).
+template <int VAR>
+__device__ __forceinline__ bool accum_tile(const StepHead &h, PairState *st, const Index &ix, const float4 *src,
+                                           const int *prev, double *resid, double *partial, int tile, int ntiles,
+                                           double *red, int *s_last) {
+    constexpr int K = VAR ? kSumsP2PL : kSumsP2P;
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    const int i = tile * kBlock + threadIdx.x;
+    if (i < h.M) accum_point<VAR>(h, ix, src, prev, resid, i, acc);
+    block_reduce_store<K>(acc, partial + (size_t)tile * K, red);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_last = (atomicAdd(&st->counter, 1u) == (unsigned)ntiles - 1u);
+    __syncthreads();
+    const bool last = *s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// Work of the block that completed a pass: the fixed-order reduction of the
+// tile records, then either the nu_max median (PH_INIT) or one solver step.
+// Resets the tile counter for the next pass.
+template <int K>
+__device__ __forceinline__ void finish_pass(const StepHead &h, PairState *st, const double *partial, int ntiles,
+                                            const double *resid, double *trace, double *sS) {
+    reduce_tiles<K>(partial, ntiles, sS);
+    if (h.phase == PH_INIT) {
+        const int n = h.M;
+        const double lo = block_kth(resid, n, (n - 1) / 2);
+        const double hi = (n % 2) ? lo : block_kth(resid, n, n / 2);
+        if (threadIdx.x == 0) {
+            st->device_steps++;
+            if (st->eval_counts) st->corr_passes++;
+            start_after_init(st, 0.5 * (lo + hi));
+        }
+    } else if (threadIdx.x == 0) {
+        solver_step(st, sS, trace);
+    }
+    if (threadIdx.x == 0) st->counter = 0u;
+    __syncthreads();
+}
+
+}  // namespace
+}  // namespace fricp

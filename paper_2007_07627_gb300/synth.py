@@ -21,7 +21,8 @@ from scipy.spatial.transform import Rotation
 
 __all__ = [
     "Pair", "rng", "random_rigid", "torus_pair", "height_field_pair",
-    "ellipsoid_pair", "config_pair", "CONFIG_SEEDS",
+    "ellipsoid_pair", "config_pair", "CONFIG_SEEDS", "BATCH_VARIANTS", "batch_pairs",
+    "serve_requests",
 ]
 
 # Seed of workload i (1-based) is 20070762 + i.
@@ -170,7 +171,7 @@ def _ellipsoid_draw(g, ep):
 # Pair assembly
 # ----------------------------------------------------------------------------
 
-def _crop_bounds(g, draw, overlap: float, dim: int):
+def _crop_bounds(g, draw, overlap: float, dim: int, pool: int = 200_000):
     """Two parallel half-spaces with `overlap` of the source inside the target's.
 
     Target keeps a.x >= s_T, source keeps a.x <= s_S; quantiles chosen so the
@@ -179,8 +180,8 @@ def _crop_bounds(g, draw, overlap: float, dim: int):
     if overlap >= 1.0:
         return None, None
     a = _unit(g.standard_normal(dim))
-    pool, _ = draw(200_000)
-    v = pool[:, :dim] @ a
+    sample, _ = draw(pool)
+    v = sample[:, :dim] @ a
     fs = 1.0 / (2.0 - overlap)
     s_T = float(np.quantile(v, 1.0 - fs))
     s_S = float(np.quantile(v, fs))
@@ -189,8 +190,8 @@ def _crop_bounds(g, draw, overlap: float, dim: int):
     return keep_T, keep_S
 
 
-def _assemble(g, draw, M, N, overlap, noise, outliers, max_angle, dim_crop, name):
-    keep_T, keep_S = _crop_bounds(g, draw, overlap, dim_crop)
+def _assemble(g, draw, M, N, overlap, noise, outliers, max_angle, dim_crop, name, pool=200_000):
+    keep_T, keep_S = _crop_bounds(g, draw, overlap, dim_crop, pool)
     Q, nQ = _fill(draw, N, keep_T, g)
     diag = float(np.linalg.norm(Q.max(0) - Q.min(0)))
     n_out = int(round(outliers * M))
@@ -208,26 +209,26 @@ def _assemble(g, draw, M, N, overlap, noise, outliers, max_angle, dim_crop, name
 
 
 def torus_pair(seed, M=2000, N=2000, overlap=1.0, noise=0.002, outliers=0.0,
-               max_angle=30.0) -> Pair:
+               max_angle=30.0, crop_pool=200_000) -> Pair:
     g = rng(seed)
     return _assemble(g, _torus_draw(g), M, N, overlap, noise, outliers, max_angle,
-                     3, "torus")
+                     3, "torus", crop_pool)
 
 
 def height_field_pair(seed, M=80_000, N=100_000, overlap=0.6, noise=0.005,
-                      outliers=0.10, max_angle=25.0) -> Pair:
+                      outliers=0.10, max_angle=25.0, crop_pool=200_000) -> Pair:
     g = rng(seed)
     hp = _height_params(g)
     return _assemble(g, _height_draw(g, hp), M, N, overlap, noise, outliers,
-                     max_angle, 2, "height_field")
+                     max_angle, 2, "height_field", crop_pool)
 
 
 def ellipsoid_pair(seed, M=200_000, N=500_000, overlap=0.5, noise=0.003,
-                   outliers=0.05, max_angle=25.0) -> Pair:
+                   outliers=0.05, max_angle=25.0, crop_pool=200_000) -> Pair:
     g = rng(seed)
     ep = _ellipsoid_params(g)
     return _assemble(g, _ellipsoid_draw(g, ep), M, N, overlap, noise, outliers,
-                     max_angle, 3, "ellipsoids")
+                     max_angle, 3, "ellipsoids", crop_pool)
 
 
 def config_pair(i: int, scale: float = 1.0) -> Pair:
@@ -240,3 +241,47 @@ def config_pair(i: int, scale: float = 1.0) -> Pair:
     if i == 3:
         return ellipsoid_pair(s, M=max(8, int(200_000 * scale)), N=max(8, int(500_000 * scale)))
     raise ValueError(f"no single-pair workload {i}")
+
+
+# ----------------------------------------------------------------------------
+# Many-pair workloads
+# ----------------------------------------------------------------------------
+
+BATCH_VARIANTS = ("p2p", "p2p_welsch", "p2pl_welsch")
+_GENERATORS = (torus_pair, height_field_pair, ellipsoid_pair)
+
+
+def _log_uniform(g, lo, hi) -> float:
+    return math.exp(g.uniform(math.log(lo), math.log(hi)))
+
+
+def batch_pairs(seed: int = CONFIG_SEEDS[4], npairs: int = 256, lo: int = 2000, hi: int = 200_000,
+                variants=BATCH_VARIANTS) -> list:
+    """Mixed batch of independent registrations: M and N each log-uniform in
+    [lo, hi], variants cycled in equal shares, surface generator uniform over
+    torus / height field / ellipsoids, overlap U[0.5, 1], outliers U[0, 0.1],
+    rotation angle up to 30 degrees; each pair has its own sub-seed (the crop
+    planes come from a sample of max(20000, M + N) surface points).
+    Returns a list of (variant, Pair)."""
+    g = rng(seed)
+    out = []
+    for k in range(npairs):
+        M = int(round(_log_uniform(g, lo, hi)))
+        N = int(round(_log_uniform(g, lo, hi)))
+        kind = int(g.integers(3))
+        overlap = float(g.uniform(0.5, 1.0))
+        outliers = float(g.uniform(0.0, 0.1))
+        sub_seed = int(g.integers(1 << 62))
+        pair = _GENERATORS[kind](sub_seed, M=M, N=N, overlap=overlap, outliers=outliers, max_angle=30.0,
+                                 crop_pool=max(20_000, M + N))
+        out.append((variants[k % len(variants)], pair))
+    return out
+
+
+def serve_requests(seed: int = CONFIG_SEEDS[5], n: int = 64, lo: int = 1000, hi: int = 1_000_000) -> list:
+    """Requests of the serving workload: robust registrations (Welsch
+    point-to-point and point-to-plane, alternating), M and N log-uniform in
+    [lo, hi], the same surface generators, overlap U[0.5, 1], outliers
+    U[0, 0.1]. Returns a list of (variant, Pair); arrival times are drawn by
+    the caller from the rate it sweeps."""
+    return batch_pairs(seed, n, lo, hi, variants=("p2p_welsch", "p2pl_welsch"))
