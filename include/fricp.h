@@ -47,7 +47,8 @@ typedef enum {
     FRICP_ETIMEOUT = 4,     /* the registration did not finish within params.timeout_s or the step budget */
     FRICP_EDEGENERATE = 5,  /* all Welsch weights vanished (sum w = 0) or the 6x6 point-to-plane
                                system is not positive definite; the last valid iterate is returned */
-    FRICP_EUNSUPPORTED = 6  /* variant needs something the target lacks (normals) */
+    FRICP_EUNSUPPORTED = 6, /* variant needs something the target lacks (normals) */
+    FRICP_EBUSY = 7         /* the server's request queue is full; step it and submit again */
 } fricp_status;
 
 typedef enum {
@@ -160,6 +161,55 @@ fricp_status fricp_batch_register(int32_t npairs, const fricp_target *const *tar
  * per SM. Any pointer may be NULL. Never fails. */
 void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_per_sm,
                             int32_t *accumulate_blocks_per_sm);
+
+/* Serving loop with continuous batching (no counterpart in the paper).
+ * Registrations are submitted at any time; fricp_server_step admits queued
+ * requests in FIFO order while a slot is free and their device buffers fit in
+ * the server's HBM budget, keeps each admitted request's state, correspondences
+ * and packed source resident on the device, and advances all of them together
+ * with the batched step of fricp_batch_register (one CUDA graph of
+ * steps_per_sync steps per replay). Admission work (staging, Morton sort,
+ * nu statistics) runs on a second stream while the step graph replays. Each
+ * served result equals, bit for bit, what fricp_register returns for the same
+ * request alone. A handle is used by one thread at a time (calls are also
+ * serialised internally). */
+typedef struct fricp_server fricp_server;
+
+/* hbm_budget: bytes of device buffers for requests in flight (0 = half of the
+ * free device memory; a request holds 28 B per source point, 224 B per
+ * 256 points and one solver state of a few KB). max_slots: requests in flight at most
+ * (1..4096). steps_per_sync: device steps per graph replay. max_queue:
+ * requests waiting for admission at most. stream: submits of device sources
+ * are ordered after the work queued on it. Errors: EINVAL, ENOMEM, ECUDA. */
+fricp_status fricp_server_create(size_t hbm_budget, int32_t max_slots, int32_t steps_per_sync,
+                                 int32_t max_queue, void *stream, fricp_server **out);
+
+/* Queue a registration (arguments as fricp_register, without the trace). The
+ * source is copied (host memory to a host buffer; device memory to a library
+ * device buffer, ordered after the server's stream), so the caller may reuse
+ * p_xyz at once; the target must stay alive until the request's result has
+ * been polled. Never blocks on the GPU. *ticket identifies the request.
+ * Errors: EINVAL (as fricp_register, or a request larger than the budget),
+ * EUNSUPPORTED, ENOMEM, ECUDA; EBUSY when max_queue requests are waiting. */
+fricp_status fricp_server_submit(fricp_server *server, const fricp_target *target, const float *p_xyz,
+                                 int64_t m, int32_t on_device, const double *T0,
+                                 const fricp_params *params, uint64_t *ticket);
+
+/* Run about nsteps device steps (rounded up to whole graph replays) for every
+ * request in flight, admit what fits from the queue (overlapping the steps),
+ * and collect the requests that finished. Blocks until the steps are done.
+ * in_flight / queued (may be NULL): counts after the call. A request whose
+ * admission fails (bad data found on the device, out of memory) finishes with
+ * that status in its result; the server carries on. Errors: EINVAL, ECUDA,
+ * ETIMEOUT. */
+fricp_status fricp_server_step(fricp_server *server, int32_t nsteps, int32_t *in_flight, int32_t *queued);
+
+/* *done = 1 and *out filled (once) when the request has finished, else
+ * *done = 0. Errors: EINVAL (NULL or a ticket never issued). */
+fricp_status fricp_server_poll(fricp_server *server, uint64_t ticket, fricp_result *out, int32_t *done);
+
+/* Wait for the server's work, free everything it holds (NULL is accepted). */
+fricp_status fricp_server_destroy(fricp_server *server);
 
 /* The correspondence step alone (Sec. 3, Eq. 3): for every x_i = R p_i + t
  * (T: double[16] row-major, NULL = identity; p_xyz device float32 [m][3]),

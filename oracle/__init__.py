@@ -325,6 +325,23 @@ class Params:
     nu_max: float = 0.0            # <= 0: paper rule
     nu_min: float = 0.0            # <= 0: paper rule
     nu_min_floor: float = NU_MIN_FLOOR
+    # Sensitivity probe, off by default (0.0 leaves every result unchanged):
+    # each alignment result (T' of Eq. 4 / Eq. 12, xi* of Eq. 19) is moved by a
+    # seeded rigid perturbation of this size in normalised units, the scale of
+    # the rounding in which two correct FP64 implementations differ. Runs with
+    # it on show how far the iteration amplifies rounding on a given input.
+    solve_jitter: float = 0.0
+    jitter_seed: int = 0
+
+
+def _jitter(params: Params):
+    """(perturb_T, perturb_xi) for Params.solve_jitter; identities when it is 0."""
+    if params.solve_jitter == 0.0:
+        return (lambda T: T), (lambda xi: xi)
+    g = np.random.default_rng(params.jitter_seed)
+    eps = params.solve_jitter
+    return (lambda T: se3_exp(se3_matrix(eps * g.standard_normal(6))) @ T), \
+           (lambda xi: xi + eps * g.standard_normal(6))
 
 
 def _result(nz, Tn, c, nu_max, nu_min, E, trace, status="ok"):
@@ -366,10 +383,12 @@ def register_point_to_point(P32, Q32, params: Params, T0=None) -> dict:
         d2 = C[1]
         return float(welsch(np.sqrt(d2), nu).sum()) if robust else float(d2.sum())
 
+    jit_T, _ = _jitter(params)
+
     def align(C, nu):
         idx, d2 = C
         w = np.exp(-d2 / (2.0 * nu * nu)) if robust else np.ones_like(d2)
-        return weighted_procrustes(Pn, Qn[idx], w)
+        return jit_T(weighted_procrustes(Pn, Qn[idx], w))
 
     T_prev = np.eye(4) if T0 is None else nz.T_to_normalized(np.asarray(T0, np.float64))
     C_prev = corr(T_prev)                                     # Q^(0)
@@ -504,6 +523,8 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
         E = float(welsch(B, nu).sum()) if nu is not None else None
         return dict(xi=np.array(xi, dtype=np.float64), idx=idx, B=B, n=n, E=E)
 
+    _, jit_xi = _jitter(params)
+
     def gn_map(ev, nu):
         """G_ppl (Eq. 19): solve the Gauss-Newton system of Eq. (18) at ev['xi'].
 
@@ -520,7 +541,7 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
             cf = sla.cho_factor(A)
         except np.linalg.LinAlgError as e:
             raise Degenerate("singular point-to-plane system") from e
-        return sla.cho_solve(cf, b)
+        return jit_xi(sla.cho_solve(cf, b))
 
     xi0 = np.zeros(6) if T0 is None else se3_vee(se3_log(nz.T_to_normalized(np.asarray(T0, np.float64))))
     ev_prev = evaluate(xi0, None)

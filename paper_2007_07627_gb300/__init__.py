@@ -24,7 +24,8 @@ __all__ = [
 
 P2P_AA, P2P_WELSCH_AA, P2PL_WELSCH_AA = 0, 1, 2
 VARIANTS = {"p2p": P2P_AA, "p2p_welsch": P2P_WELSCH_AA, "p2pl_welsch": P2PL_WELSCH_AA}
-STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EDEGENERATE", 6: "EUNSUPPORTED"}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EDEGENERATE", 6: "EUNSUPPORTED",
+          7: "EBUSY"}
 
 _PKG = pathlib.Path(__file__).resolve().parent
 _LIB_PATH = _PKG / "libfricp.so"
@@ -93,9 +94,16 @@ def lib() -> ctypes.CDLL:
     L.fricp_batch_register.argtypes = [i32, pp, pp, ctypes.POINTER(i64), i32, dp, ctypes.POINTER(Params), vp,
                                        ctypes.POINTER(Result), dp, i32]
     L.fricp_batch_last_shape.argtypes = [ctypes.POINTER(i32)] * 3
+    L.fricp_server_create.argtypes = [ctypes.c_size_t, i32, i32, i32, vp, ctypes.POINTER(vp)]
+    L.fricp_server_submit.argtypes = [vp, vp, vp, i64, i32, dp, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)]
+    L.fricp_server_step.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.fricp_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result), ctypes.POINTER(i32)]
+    L.fricp_server_destroy.argtypes = [vp]
     L.fricp_batch_last_shape.restype = None
     for name in ("fricp_params_default", "fricp_target_create", "fricp_target_destroy", "fricp_register",
-                 "fricp_closest_points", "fricp_eval_pass", "fricp_target_nu_min", "fricp_batch_register"):
+                 "fricp_closest_points", "fricp_eval_pass", "fricp_target_nu_min", "fricp_batch_register",
+                 "fricp_server_create", "fricp_server_submit", "fricp_server_step", "fricp_server_poll",
+                 "fricp_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -268,6 +276,52 @@ def batch_last_shape() -> dict:
     c, a, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     lib().fricp_batch_last_shape(ctypes.byref(c), ctypes.byref(a), ctypes.byref(b))
     return {"chunk": c.value, "search_blocks_per_sm": a.value, "accumulate_blocks_per_sm": b.value}
+
+
+class Server:
+    """Serving loop with continuous batching (fricp_server_*)."""
+
+    def __init__(self, hbm_budget: int = 0, max_slots: int = 256, steps_per_sync: int = 16, max_queue: int = 4096,
+                 stream=None):
+        out = ctypes.c_void_p()
+        _check(lib().fricp_server_create(int(hbm_budget), int(max_slots), int(steps_per_sync), int(max_queue),
+                                         _stream(stream), ctypes.byref(out)))
+        self.handle = out.value
+
+    def submit(self, target: Target, p, params: Params | None = None, T0=None) -> int:
+        """Queue a registration; returns its ticket. Raises FricpError (EBUSY) when the queue is full."""
+        if params is None:
+            params = params_default()
+        pp, m, dev, pk = _points(p)
+        Tp, Tk = _mat(T0)
+        ticket = ctypes.c_uint64()
+        _check(lib().fricp_server_submit(self.handle, target.handle, pp, m, dev, Tp, ctypes.byref(params),
+                                         ctypes.byref(ticket)))
+        return ticket.value
+
+    def step(self, nsteps: int = 16) -> tuple:
+        """Advance every request in flight; returns (in_flight, queued)."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().fricp_server_step(self.handle, int(nsteps), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def poll(self, ticket: int):
+        """The request's result dict once it has finished (returned once), else None."""
+        r = Result()
+        done = ctypes.c_int32()
+        _check(lib().fricp_server_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r), ctypes.byref(done)))
+        return _result(r) if done.value else None
+
+    def destroy(self):
+        if self.handle:
+            lib().fricp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def closest_points(target: Target, p, T=None, stream=None):

@@ -641,3 +641,298 @@ extern "C" void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_pe
     if (search_blocks_per_sm) *search_blocks_per_sm = fricp::g_last_shape.nn_per_sm;
     if (accumulate_blocks_per_sm) *accumulate_blocks_per_sm = fricp::g_last_shape.acc_per_sm;
 }
+
+// ---------------------------------------------------------------------------
+// Serving loop: continuous batching over the batched step engine.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    const fricp_target *target = nullptr;
+    std::vector<float> host_pts;   // copy of a host source
+    float *dev_pts = nullptr;      // library copy of a device source
+    int64_t m = 0;
+    bool has_T0 = false;
+    double T0[16];
+    fricp_params prm;
+    size_t bytes = 0;              // device buffers while in flight
+};
+
+struct Running {
+    Request req;
+    PairBuffers buf;
+    double scale = 1.0, c[3] = {0, 0, 0};
+};
+
+}  // namespace
+
+struct fricp_server {
+    BatchEngine eng;
+    cudaStream_t s_step = nullptr, s_admit = nullptr, user = nullptr;
+    cudaEvent_t ev_admit = nullptr, ev_user = nullptr, poll = nullptr;
+    size_t budget = 0, used = 0;
+    int max_slots = 0;
+    int steps_per_graph = 16;
+    int max_queue = 0;
+    bool tuned = false;
+    double timeout_s = 600.0;
+    std::deque<Request> queue;
+    std::vector<std::unique_ptr<Running>> slots;
+    std::map<uint64_t, fricp_result> finished;
+    uint64_t next_ticket = 1;
+    std::mutex mu;
+};
+
+namespace {
+
+// Admission of the queue's head requests that fit (FIFO, a free slot and room
+// in the budget): heavy work on s_admit, then the commit of each one on s_step
+// (after everything already queued there).
+fricp_status admit_queued(fricp_server *sv, int *admitted) {
+    *admitted = 0;
+    while (!sv->queue.empty()) {
+        Request &rq = sv->queue.front();
+        if (sv->used + rq.bytes > sv->budget) break;
+        int slot = -1;
+        for (int p = 0; p < sv->max_slots; ++p)
+            if (!sv->slots[p]) {
+                slot = p;
+                break;
+            }
+        if (slot < 0) break;
+        auto run = std::make_unique<Running>();
+        run->req = std::move(rq);
+        sv->queue.pop_front();
+        Request &r = run->req;
+        PairState h;
+        fricp::Slot sl;
+        const float *src = r.dev_pts ? r.dev_pts : r.host_pts.data();
+        fricp_status st = admit_pair(r.target, src, r.m, r.dev_pts != nullptr, r.has_T0 ? r.T0 : nullptr, r.prm, 0,
+                                     sv->s_admit, &run->buf, &h, &run->scale, run->c, &sl);
+        if (st != FRICP_OK) {   // the request fails alone; the server carries on
+            fricp_result res;
+            std::memset(&res, 0, sizeof(res));
+            res.status = st;
+            sv->finished[r.ticket] = res;
+            run->buf.free(sv->s_admit);
+            if (r.dev_pts) cudaFreeAsync(r.dev_pts, sv->s_admit);
+            continue;
+        }
+        cudaError_t e = cudaEventRecord(sv->ev_admit, sv->s_admit);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->s_step, sv->ev_admit, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(run->buf.st, &h, sizeof(PairState), cudaMemcpyHostToDevice, sv->s_step);
+        if (e == cudaSuccess) e = cudaMemsetAsync(run->buf.prev, 0xff, sizeof(int) * r.m, sv->s_step);
+        if (e == cudaSuccess) e = sv->eng.upload_slot(slot, sl);
+        counters().h2d += sizeof(PairState);
+        if (e != cudaSuccess) return cuda_fail(e, "admitting a request");
+        if (r.dev_pts) {
+            cudaFreeAsync(r.dev_pts, sv->s_step);
+            r.dev_pts = nullptr;
+        }
+        r.host_pts.clear();
+        r.host_pts.shrink_to_fit();
+        sv->used += r.bytes;
+        sv->slots[slot] = std::move(run);
+        ++*admitted;
+    }
+    return FRICP_OK;
+}
+
+// Results of the slots the last plan reported done: read, convert, free.
+fricp_status harvest(fricp_server *sv) {
+    std::vector<int> ready;
+    for (int p = 0; p < sv->max_slots; ++p)
+        if (sv->slots[p] && sv->eng.h_done[p]) ready.push_back(p);
+    if (ready.empty()) return FRICP_OK;
+    std::vector<PairState> states(ready.size());
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < ready.size() && e == cudaSuccess; ++k) {
+        e = cudaMemcpyAsync(&states[k], sv->slots[ready[k]]->buf.st, sizeof(PairState), cudaMemcpyDeviceToHost,
+                            sv->s_step);
+        counters().d2h += sizeof(PairState);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sv->s_step);
+    if (e != cudaSuccess) return cuda_fail(e, "reading finished requests");
+    fricp::Slot empty;
+    std::memset(&empty, 0, sizeof(empty));
+    for (size_t k = 0; k < ready.size(); ++k) {
+        const int p = ready[k];
+        Running &run = *sv->slots[p];
+        fricp_result res;
+        std::memset(&res, 0, sizeof(res));
+        fill_result(states[k], run.req.prm.variant, run.scale, run.c, 0, &res);
+        sv->finished[run.req.ticket] = res;
+        e = sv->eng.upload_slot(p, empty);   // stream-ordered before the buffers are freed and reused
+        if (e != cudaSuccess) return cuda_fail(e, "releasing a slot");
+        run.buf.free(sv->s_step);
+        sv->used -= run.req.bytes;
+        sv->slots[p].reset();
+    }
+    return FRICP_OK;
+}
+
+int count_in_flight(const fricp_server *sv) {
+    int n = 0;
+    for (const auto &r : sv->slots) n += r != nullptr;
+    return n;
+}
+
+}  // namespace
+
+extern "C" fricp_status fricp_server_create(size_t hbm_budget, int32_t max_slots, int32_t steps_per_sync,
+                                            int32_t max_queue, void *stream, fricp_server **out) {
+    if (!out) return fail(FRICP_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > fricp::kMaxSlots) return fail(FRICP_EINVAL, "max_slots must be in 1..4096");
+    if (steps_per_sync < 1 || steps_per_sync > 4096) return fail(FRICP_EINVAL, "steps_per_sync in 1..4096");
+    if (max_queue < 1) return fail(FRICP_EINVAL, "max_queue must be >= 1");
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return cuda_fail(e, "querying device memory");
+    if (hbm_budget == 0) hbm_budget = free_b / 2;
+    if (hbm_budget > free_b) return fail(FRICP_EINVAL, "hbm_budget exceeds free device memory");
+    auto sv = std::make_unique<fricp_server>();
+    sv->budget = hbm_budget;
+    sv->max_slots = max_slots;
+    sv->steps_per_graph = steps_per_sync;
+    sv->max_queue = max_queue;
+    sv->user = (cudaStream_t)stream;
+    sv->slots.resize(max_slots);
+    e = cudaStreamCreateWithFlags(&sv->s_step, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->s_admit, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_admit, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_user, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->poll, cudaEventDisableTiming);
+    // the tile list holds every tile the budget can keep in flight, plus one per slot
+    const int64_t max_points = (int64_t)(hbm_budget / (sizeof(float4) + sizeof(int) + sizeof(double))) + 1;
+    const int64_t tiles = max_points / fricp::kBlock + max_slots + 1;
+    if (e == cudaSuccess) e = sv->eng.init(max_slots, (int)std::min<int64_t>(tiles, 1 << 30), sv->s_step);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sv->s_step);
+    if (e != cudaSuccess) {
+        fricp_server *raw = sv.release();
+        fricp_server_destroy(raw);
+        return cuda_fail(e, "creating the server");
+    }
+    *out = sv.release();
+    return FRICP_OK;
+}
+
+extern "C" fricp_status fricp_server_submit(fricp_server *sv, const fricp_target *target, const float *p_xyz,
+                                            int64_t m, int32_t on_device, const double *T0,
+                                            const fricp_params *params, uint64_t *ticket) {
+    if (!sv || !ticket) return fail(FRICP_EINVAL, "NULL argument");
+    fricp_status st = check_pair(target, p_xyz, m, T0, params);
+    if (st != FRICP_OK) return st;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if ((int)sv->queue.size() >= sv->max_queue) return fail(FRICP_EBUSY, "request queue is full");
+    Request r;
+    r.target = target;
+    r.m = m;
+    r.prm = *params;
+    r.has_T0 = T0 != nullptr;
+    if (T0) std::memcpy(r.T0, T0, sizeof(r.T0));
+    r.bytes = PairBuffers::need(m, 0);
+    if (r.bytes > sv->budget) return fail(FRICP_EINVAL, "request needs more device memory than the server budget");
+    if (on_device) {
+        cudaError_t e = cudaEventRecord(sv->ev_user, sv->user);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->s_admit, sv->ev_user, 0);
+        if (e == cudaSuccess) e = cudaMallocAsync(&r.dev_pts, sizeof(float) * 3 * m, sv->s_admit);
+        if (e != cudaSuccess) return fail(FRICP_ENOMEM, "device copy of a request");
+        e = cudaMemcpyAsync(r.dev_pts, p_xyz, sizeof(float) * 3 * m, cudaMemcpyDeviceToDevice, sv->s_admit);
+        if (e == cudaSuccess) e = cudaEventRecord(sv->ev_user, sv->s_admit);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->user, sv->ev_user, 0);   // caller may reuse p_xyz after it
+        if (e != cudaSuccess) return cuda_fail(e, "copying a request");
+    } else {
+        if (!host_finite(p_xyz, 3 * m)) return fail(FRICP_EINVAL, "p_xyz has NaN or Inf");
+        r.host_pts.assign(p_xyz, p_xyz + 3 * m);
+    }
+    r.ticket = sv->next_ticket++;
+    *ticket = r.ticket;
+    sv->queue.push_back(std::move(r));
+    return FRICP_OK;
+}
+
+extern "C" fricp_status fricp_server_step(fricp_server *sv, int32_t nsteps, int32_t *in_flight, int32_t *queued) {
+    if (!sv) return fail(FRICP_EINVAL, "NULL argument");
+    if (nsteps < 0) return fail(FRICP_EINVAL, "nsteps must be >= 0");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    int admitted = 0;
+    fricp_status st = FRICP_OK;
+    if (!sv->tuned) {
+        st = admit_queued(sv, &admitted);
+        if (st != FRICP_OK) return st;
+        if (admitted > 0) {
+            int64_t pts = 0;
+            int tiles = 0;
+            for (const auto &r : sv->slots)
+                if (r) {
+                    pts += r->req.m;
+                    tiles += (int)((r->req.m + fricp::kBlock - 1) / fricp::kBlock);
+                }
+            cudaError_t e = sv->eng.tune(pts, count_in_flight(sv), tiles);
+            if (e == cudaSuccess) e = sv->eng.capture(sv->steps_per_graph);
+            if (e != cudaSuccess) return cuda_fail(e, "tuning the served step");
+            sv->tuned = true;
+        }
+    }
+    const int graphs = sv->tuned && count_in_flight(sv) > 0 ? (nsteps + sv->steps_per_graph - 1) / sv->steps_per_graph : 0;
+    for (int k = 0; k < graphs; ++k) {
+        const cudaError_t e = sv->eng.run_graph();
+        if (e != cudaSuccess) return cuda_fail(e, "running the served step");
+    }
+    // admission overlaps the steps just launched
+    st = admit_queued(sv, &admitted);
+    if (st != FRICP_OK) return st;
+    cudaError_t e = sv->eng.fetch_status();
+    if (e == cudaSuccess) e = cudaEventRecord(sv->poll, sv->s_step);
+    if (e != cudaSuccess) return cuda_fail(e, "polling the served step");
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                              std::chrono::duration<double>(sv->timeout_s));
+    st = wait_event(sv->poll, deadline);
+    if (st != FRICP_OK) return st;
+    if (sv->eng.h_ctl->overflow) return fail(FRICP_ECUDA, "served tile list overflow");
+    if (graphs > 0) {   // the done flags describe the state after the launched steps
+        st = harvest(sv);
+        if (st != FRICP_OK) return st;
+    }
+    if (in_flight) *in_flight = count_in_flight(sv);
+    if (queued) *queued = (int32_t)sv->queue.size();
+    return FRICP_OK;
+}
+
+extern "C" fricp_status fricp_server_poll(fricp_server *sv, uint64_t ticket, fricp_result *out, int32_t *done) {
+    if (!sv || !out || !done) return fail(FRICP_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->finished.find(ticket);
+    if (it == sv->finished.end()) {
+        *done = 0;
+        if (ticket == 0 || ticket >= sv->next_ticket) return fail(FRICP_EINVAL, "unknown ticket");
+        return FRICP_OK;
+    }
+    *out = it->second;
+    *done = 1;
+    sv->finished.erase(it);
+    return FRICP_OK;
+}
+
+extern "C" fricp_status fricp_server_destroy(fricp_server *sv) {
+    if (!sv) return FRICP_OK;
+    if (sv->s_step) cudaStreamSynchronize(sv->s_step);
+    if (sv->s_admit) cudaStreamSynchronize(sv->s_admit);
+    for (auto &r : sv->slots)
+        if (r) r->buf.free(sv->s_step);
+    for (auto &r : sv->queue)
+        if (r.dev_pts) cudaFreeAsync(r.dev_pts, sv->s_step);
+    if (sv->s_step) cudaStreamSynchronize(sv->s_step);
+    sv->eng.release();
+    if (sv->ev_admit) cudaEventDestroy(sv->ev_admit);
+    if (sv->ev_user) cudaEventDestroy(sv->ev_user);
+    if (sv->poll) cudaEventDestroy(sv->poll);
+    if (sv->s_step) cudaStreamDestroy(sv->s_step);
+    if (sv->s_admit) cudaStreamDestroy(sv->s_admit);
+    delete sv;
+    return FRICP_OK;
+}

@@ -84,18 +84,23 @@ def _permuted(pair, seed):
     return pair.P[perm]
 
 
-def oracle_reference(pair, variant, over, perms=(1, 2)):
+def oracle_reference(pair, variant, over, perms=(1, 2), jitters=0, jitter=1e-13):
     """Oracle run plus runs on permuted copies of the source (a permutation only
-    changes the FP64 summation order). Returns the base result, whether the
-    oracle is stable under its own rounding (equal counters), the first trace
-    index where a permuted run departs by more than 1e-9 relative (the oracle's
-    own chaos horizon) and the spread of the final transforms."""
+    changes the FP64 summation order) and `jitters` runs whose alignment solves
+    carry a seeded rigid perturbation of size `jitter` (the rounding scale at
+    which two correct FP64 implementations differ). Returns the base result,
+    whether the oracle is stable under these perturbations (equal counters), the
+    first trace index where a perturbed run departs by more than 1e-9 relative
+    (the oracle's own chaos horizon) and the spread of the final transforms."""
+    import dataclasses
     import oracle
     prm = oracle.Params(variant=variant, **over)
     base = oracle.register(pair.P, pair.Q, prm, normals=pair.normals)
     stable, horizon, spread_ang, spread_t, energies = True, len(base["trace"]), 0.0, 0.0, [base["final_energy"]]
-    for s in perms:
-        r = oracle.register(_permuted(pair, s), pair.Q, prm, normals=pair.normals)
+    runs = [(_permuted(pair, s), prm) for s in perms]
+    runs += [(pair.P, dataclasses.replace(prm, solve_jitter=jitter, jitter_seed=s)) for s in range(1, jitters + 1)]
+    for P, prm_k in runs:
+        r = oracle.register(P, pair.Q, prm_k, normals=pair.normals)
         for key in ("iterations", "corr_passes", "reverts", "line_search_trials", "stages"):
             stable &= r[key] == base[key]
         n = min(len(r["trace"]), len(base["trace"]))

@@ -71,10 +71,12 @@ def test_batch_matches_oracle(fr, small_batch):
     res = fr.batch_register(targets, [p.P for _, p in small_batch], prms, trace_capacity=4096)
     for (v, p), r in zip(small_batch, res):
         over = {"max_iters": 100} if v == "p2p" else {}
-        # eight permuted oracle runs: small robust pairs can sit on a near-tied
-        # decision that the summation order alone flips (one of pair 5's
-        # permutations takes the GPU's branch, with the same iteration count)
-        ref = oracle_reference(p, v, over, perms=tuple(range(1, 9)))
+        # Small robust pairs near nu_min can make the point-to-plane normal
+        # equations so ill-conditioned that rounding-level differences grow a
+        # million-fold in one step (pair 5 at its sixth nu stage); the oracle's
+        # spread is therefore measured over permuted sources and over runs with
+        # rounding-scale perturbations of the alignment solves.
+        ref = oracle_reference(p, v, over, perms=(1, 2, 3, 4), jitters=4)
         assert_registration_parity(r, ref, p.diag)
     for t in targets:
         t.destroy()

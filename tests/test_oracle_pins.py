@@ -389,3 +389,21 @@ def test_normalization_round_trip():
     assert np.abs(oracle.apply(Tn, nz.fwd(P)) - nz.fwd(oracle.apply(T, P))).max() < 1e-12
     both = np.concatenate([nz.fwd(P), nz.fwd(Q)])
     assert np.linalg.norm(both.max(0) - both.min(0)) == pytest.approx(1.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch", "p2pl_welsch"])
+def test_solve_jitter_is_off_by_default_and_small_on_a_well_posed_case(variant):
+    """The sensitivity probe leaves the oracle unchanged at 0, and on a
+    well-conditioned exact copy a 1e-13 perturbation of every alignment solve
+    moves the answer by rounding-level amounts only (so a large spread under it
+    is a property of the input, not of the probe)."""
+    import dataclasses
+    P, Q, N, R, t = _surface_pair(19, n=600, angle=0.1)
+    prm = oracle.Params(variant=variant)
+    a = oracle.register(P, Q, prm, normals=N)
+    b = oracle.register(P, Q, dataclasses.replace(prm, solve_jitter=0.0, jitter_seed=5), normals=N)
+    assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["t"], b["t"])
+    assert a["iterations"] == b["iterations"]
+    c = oracle.register(P, Q, dataclasses.replace(prm, solve_jitter=1e-13, jitter_seed=5), normals=N)
+    assert np.abs(c["R"] - a["R"]).max() < 1e-10
+    assert np.abs(c["t"] - a["t"]).max() < 1e-10
