@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "fricp_internal.cuh"
@@ -189,108 +190,206 @@ __global__ void k_level_boxes(float4 *__restrict__ nodes, int first, int count) 
 // original index). Per point: the median of the six distances (Sec. 4.3) and,
 // with normals, the median of the six distances to the point's tangent plane
 // (Sec. 5); the median of six is the mean of the 3rd and 4th smallest.
-__global__ void k_knn6_stats(Index ix, double *__restrict__ stat_d, double *__restrict__ stat_h) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ix.n) return;
-    const float4 qi = ix.pts[i];
-    const double x0 = qi.x, x1 = qi.y, x2 = qi.z;
-    double bd[6];
-    int bo[6], bj[6];
+//
+// One warp per query point, the traversal of warp_nn: the query's own bucket
+// is scanned first, then the siblings of its path to the root and what they
+// open, two tree levels per round; lanes test boxes and bucket points in
+// parallel. Pruning is in float: a box or candidate is skipped only when its
+// float squared distance, shrunk by kShrink (far more than the float rounding
+// of either), exceeds the current sixth-best FP64 distance rounded up to float.
+// Every point that can enter the six gets its exact FP64 distance, and the six
+// (kept identical in every lane) are merged one at a time in a fixed order, so
+// the selection and the medians are exact.
+struct Best6 {
+    double d[6];
+    int o[6], j[6];
+    float bound;   // d[5] rounded up to float
+};
+
+__device__ __forceinline__ void best6_insert(Best6 &b, double d, int o, int j) {
+    if (!(d < b.d[5] || (d == b.d[5] && o < b.o[5]))) return;
+    int s = 5;
+    while (s > 0 && (b.d[s - 1] > d || (b.d[s - 1] == d && b.o[s - 1] > o))) {
+        b.d[s] = b.d[s - 1];
+        b.o[s] = b.o[s - 1];
+        b.j[s] = b.j[s - 1];
+        --s;
+    }
+    b.d[s] = d;
+    b.o[s] = o;
+    b.j[s] = j;
+    b.bound = __double2float_ru(b.d[5]);
+}
+
+// Offers bucket na's points (lanes 0-15) and, if `two`, bucket nb's (lanes
+// 16-31) to the six; the point i itself is skipped.
+__device__ __forceinline__ void knn6_scan(const Index &ix, int i, const float xq[3], Best6 &b, int na, int nb,
+                                          bool two) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    bool cand = false;
+    double d = 0.0;
+    int o = 0, j = -1;
+    if (lane < 16 || two) {
+        j = ((lane < 16 ? na : nb) - ix.L) * kLeaf + (lane & 15);
+        if (j < ix.n && j != i) {
+            const float4 q = __ldg(ix.pts + j);
+            const float fx = q.x - xq[0], fy = q.y - xq[1], fz = q.z - xq[2];
+            if (fmaf(fz, fz, fmaf(fy, fy, fx * fx)) * kShrink <= b.bound) {
+                const double a0 = (double)q.x - (double)xq[0], a1 = (double)q.y - (double)xq[1],
+                             a2 = (double)q.z - (double)xq[2];
+                d = a0 * a0 + a1 * a1 + a2 * a2;
+                o = __float_as_int(q.w);
+                cand = true;
+            }
+        }
+    }
+    unsigned cm = __ballot_sync(FULL, cand);
+    while (cm) {   // merge in lane order: every lane applies the same insertions
+        const int src = __ffs(cm) - 1;
+        cm &= cm - 1u;
+        const double dv = __shfl_sync(FULL, d, src);
+        const int ov = __shfl_sync(FULL, o, src), jv = __shfl_sync(FULL, j, src);
+        best6_insert(b, dv, ov, jv);
+    }
+}
+
+// Returns false if the stack would overflow.
+__device__ bool warp_knn6(const Index &ix, int i, const float xq[3], Best6 &b, int *stk) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
     for (int s = 0; s < 6; ++s) {
-        bd[s] = INFINITY;
-        bo[s] = 0x7fffffff;
-        bj[s] = -1;
+        b.d[s] = INFINITY;
+        b.o[s] = 0x7fffffff;
+        b.j[s] = -1;
     }
-    int stk[kStack];
-    double stkd[kStack];
-    int sp = 0, node = 1;
-    for (;;) {
-        if (node < ix.L) {
-            const float4 *b = ix.nodes + 4 * node;
-            double d[2];
-            for (int c = 0; c < 2; ++c) {
-                const float4 lo = b[2 * c], hi = b[2 * c + 1];
-                const double g0 = fmax(fmax((double)lo.x - x0, x0 - (double)hi.x), 0.0);
-                const double g1 = fmax(fmax((double)lo.y - x1, x1 - (double)hi.y), 0.0);
-                const double g2 = fmax(fmax((double)lo.z - x2, x2 - (double)hi.z), 0.0);
-                d[c] = g0 * g0 + g1 * g1 + g2 * g2;
-            }
-            int c0 = 2 * node, c1 = c0 + 1;
-            double d0 = d[0], d1 = d[1];
-            if (d1 < d0) {
-                const double t = d0; d0 = d1; d1 = t;
-                const int tc = c0; c0 = c1; c1 = tc;
-            }
-            if (d0 * (1.0 - 1e-12) <= bd[5]) {
-                if (d1 * (1.0 - 1e-12) <= bd[5]) {
-                    stk[sp] = c1;
-                    stkd[sp] = d1;
-                    ++sp;
-                }
-                node = c0;
-                continue;
-            }
-        } else {
-            const int beg = (node - ix.L) * kLeaf;
-            const int end = min(beg + kLeaf, ix.n);
-            for (int j = beg; j < end; ++j) {
-                if (j == i) continue;
-                const float4 q = ix.pts[j];
-                const double a = (double)q.x - x0, b = (double)q.y - x1, c = (double)q.z - x2;
-                const double d = a * a + b * b + c * c;
-                const int o = __float_as_int(q.w);
-                if (d < bd[5] || (d == bd[5] && o < bo[5])) {
-                    int s = 5;
-                    while (s > 0 && (bd[s - 1] > d || (bd[s - 1] == d && bo[s - 1] > o))) {
-                        bd[s] = bd[s - 1];
-                        bo[s] = bo[s - 1];
-                        bj[s] = bj[s - 1];
-                        --s;
+    b.bound = INFINITY;
+    int depth = 0;
+    while ((1 << depth) < ix.L) ++depth;
+    // the query's own bucket and its sibling bucket first: a tight bound early
+    const int start = ix.L + i / kLeaf;
+    knn6_scan(ix, i, xq, b, start, start ^ 1, depth > 0);   // a one-bucket tree has no sibling
+    int sp;
+    {
+        int c = 0;
+        bool pass = false;
+        if (lane < depth - 1) {   // the sibling of the path node at level lane + 1 (the bucket level is done)
+            c = (start >> (depth - 1 - lane)) ^ 1;
+            pass = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), xq, zero) * kShrink <= b.bound;
+        }
+        const unsigned m = __ballot_sync(FULL, pass);
+        if (pass) stk[__popc(m & below)] = c;
+        sp = __popc(m);
+    }
+    __syncwarp();
+    const int leaf_parent_level = depth - 1;
+    while (sp > 0) {
+        const int k = min(32, sp);
+        const int node = (lane < k) ? stk[sp - 1 - lane] : 0;
+        sp -= k;
+        __syncwarp();
+        int c[4] = {0, 0, 0, 0};
+        bool ok[4] = {false, false, false, false};
+        bool leaf_ok = false;
+        if (node != 0) {
+            if (node < ix.L) {
+                const int level = 31 - __clz(node);
+                if (level < leaf_parent_level) {
+                    const float4 *bx = ix.nodes + 8 * node;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        c[g] = 4 * node + g;
+                        ok[g] = box_d2(__ldg(bx + 2 * g), __ldg(bx + 2 * g + 1), xq, zero) * kShrink <= b.bound;
                     }
-                    bd[s] = d;
-                    bo[s] = o;
-                    bj[s] = j;
+                } else {
+                    const float4 *bx = ix.nodes + 4 * node;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        c[g] = 2 * node + g;
+                        ok[g] = box_d2(__ldg(bx + 2 * g), __ldg(bx + 2 * g + 1), xq, zero) * kShrink <= b.bound;
+                    }
                 }
+            } else {
+                leaf_ok = box_d2(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), xq, zero) * kShrink
+                          <= b.bound;
             }
         }
-        node = 0;
-        while (sp > 0) {
-            --sp;
-            if (stkd[sp] * (1.0 - 1e-12) <= bd[5]) {
-                node = stk[sp];
-                break;
-            }
+        int base = sp;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const unsigned mg = __ballot_sync(FULL, ok[g]);
+            if (base + __popc(mg) > kWarpStack) return false;
+            if (ok[g]) stk[base + __popc(mg & below)] = c[g];
+            base += __popc(mg);
         }
-        if (node == 0) break;
+        sp = base;
+        unsigned lm = __ballot_sync(FULL, leaf_ok);
+        while (lm) {   // two buckets per pass: lanes 0-15 and 16-31
+            const int la = __ffs(lm) - 1;
+            lm &= lm - 1u;
+            int lb = la;
+            bool two = false;
+            if (lm) {
+                lb = __ffs(lm) - 1;
+                lm &= lm - 1u;
+                two = true;
+            }
+            const int na = __shfl_sync(FULL, node, la), nb = __shfl_sync(FULL, node, lb);
+            knn6_scan(ix, i, xq, b, na, nb, two);
+        }
+        __syncwarp();
     }
-    stat_d[i] = 0.5 * (sqrt(bd[2]) + sqrt(bd[3]));
-    if (stat_h != nullptr) {
-        const float4 ni = ix.nrm[i];
-        double h[6];
-        for (int s = 0; s < 6; ++s) {
-            if (bj[s] < 0) {
-                h[s] = INFINITY;
-                continue;
-            }
-            const float4 q = ix.pts[bj[s]];
-            h[s] = fabs(((double)q.x - x0) * ni.x + ((double)q.y - x1) * ni.y + ((double)q.z - x2) * ni.z);
+    return true;
+}
+
+constexpr int kKnnBlock = 128;
+
+__global__ void __launch_bounds__(kKnnBlock) k_knn6_stats(Index ix, double *__restrict__ stat_d,
+                                                          double *__restrict__ stat_h, int *__restrict__ overflow) {
+    __shared__ int s_stk[kKnnBlock / 32][kWarpStack];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int wpb = kKnnBlock / 32;
+    for (int i = blockIdx.x * wpb + w; i < ix.n; i += gridDim.x * wpb) {
+        const float4 qi = __ldg(ix.pts + i);
+        const float xq[3] = {qi.x, qi.y, qi.z};
+        Best6 b;
+        if (!warp_knn6(ix, i, xq, b, s_stk[w])) {
+            if (lane == 0) *overflow = 1;
+            continue;
         }
-        for (int a = 1; a < 6; ++a) {   // insertion sort of six values
-            const double v = h[a];
-            int b = a - 1;
-            while (b >= 0 && h[b] > v) {
-                h[b + 1] = h[b];
-                --b;
+        if (lane != 0) continue;
+        const double x0 = xq[0], x1 = xq[1], x2 = xq[2];
+        stat_d[i] = 0.5 * (sqrt(b.d[2]) + sqrt(b.d[3]));
+        if (stat_h != nullptr) {
+            const float4 ni = ix.nrm[i];
+            double h[6];
+            for (int s = 0; s < 6; ++s) {
+                if (b.j[s] < 0) {
+                    h[s] = INFINITY;
+                    continue;
+                }
+                const float4 q = ix.pts[b.j[s]];
+                h[s] = fabs(((double)q.x - x0) * ni.x + ((double)q.y - x1) * ni.y + ((double)q.z - x2) * ni.z);
             }
-            h[b + 1] = v;
+            for (int a = 1; a < 6; ++a) {   // insertion sort of six values
+                const double v = h[a];
+                int c = a - 1;
+                while (c >= 0 && h[c] > v) {
+                    h[c + 1] = h[c];
+                    --c;
+                }
+                h[c + 1] = v;
+            }
+            stat_h[i] = 0.5 * (h[2] + h[3]);
         }
-        stat_h[i] = 0.5 * (h[2] + h[3]);
     }
 }
 
 __global__ void k_median(const double *v, int n, double *out) {
-    const double a = block_kth(v, n, (n - 1) / 2);
-    const double b = (n % 2) ? a : block_kth(v, n, n / 2);
+    double a, b;
+    block_median_pair(v, n, &a, &b);
     if (threadIdx.x == 0) *out = 0.5 * (a + b);
 }
 
@@ -437,20 +536,30 @@ cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
     double *sd = nullptr, *sh = nullptr, *out = nullptr;
     cudaError_t e = cudaMallocAsync(&sd, sizeof(double) * t->n, s);
     if (e == cudaSuccess && t->has_normals) e = cudaMallocAsync(&sh, sizeof(double) * t->n, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&out, 2 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&out, 3 * sizeof(double), s);
+    int *flag = reinterpret_cast<int *>(out + 2);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, 3 * sizeof(double), s);
     if (e == cudaSuccess) {
         const Index ix = make_index(*t);
-        k_knn6_stats<<<(unsigned)((t->n + 127) / 128), 128, 0, s>>>(ix, sd, sh);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t blocks = std::min<int64_t>((t->n + kKnnBlock / 32 - 1) / (kKnnBlock / 32),
+                                                 (int64_t)(sms > 0 ? sms : 152) * 16);
+        k_knn6_stats<<<(unsigned)blocks, kKnnBlock, 0, s>>>(ix, sd, sh, flag);
         k_median<<<1, 1024, 0, s>>>(sd, (int)t->n, out);
         counters().launches += 2;
         if (sh) {
             k_median<<<1, 1024, 0, s>>>(sh, (int)t->n, out + 1);
             counters().launches += 1;
         }
-        double h[2] = {0.0, 0.0};
-        e = cudaMemcpyAsync(h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
-        counters().d2h += 2 * sizeof(double);
+        double h[3] = {0.0, 0.0, 0.0};
+        e = cudaMemcpyAsync(h, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        counters().d2h += 3 * sizeof(double);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        int overflow = 0;
+        std::memcpy(&overflow, &h[2], sizeof(int));
+        if (e == cudaSuccess && overflow) e = cudaErrorLaunchOutOfResources;   // search stack: never expected
         if (e == cudaSuccess) {
             t->E_Q = h[0];
             t->H_Q = sh ? h[1] : -1.0;

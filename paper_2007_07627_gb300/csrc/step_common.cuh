@@ -217,8 +217,8 @@ __device__ __forceinline__ void finish_pass(const StepHead &h, PairState *st, co
     reduce_tiles<K>(partial, ntiles, sS);
     if (h.phase == PH_INIT) {
         const int n = h.M;
-        const double lo = block_kth(resid, n, (n - 1) / 2);
-        const double hi = (n % 2) ? lo : block_kth(resid, n, n / 2);
+        double lo, hi;
+        block_median_pair(resid, n, &lo, &hi);
         if (threadIdx.x == 0) {
             st->device_steps++;
             if (st->eval_counts) st->corr_passes++;

@@ -137,6 +137,36 @@ def test_nu_min_matches_oracle(fr, variant):
     assert got == pytest.approx(ref, rel=1e-9)
 
 
+@pytest.mark.parametrize("n,dups", [(7, 0), (16, 0), (17, 3), (33, 0), (300, 40), (5000, 0)])
+def test_nu_min_small_ragged_and_duplicate_targets(fr, n, dups):
+    """One-bucket and two-bucket trees, ragged last buckets and duplicated
+    points (distance zero counts as a neighbour)."""
+    g = np.random.default_rng(n + dups)
+    Q = g.random((n, 3)).astype(np.float32)
+    if dups:
+        Q[n - dups:] = Q[g.integers(0, n - dups, dups)]
+    Nrm = g.standard_normal((n, 3))
+    Nrm = (Nrm / np.linalg.norm(Nrm, axis=1, keepdims=True)).astype(np.float32)
+    t = fr.target_create(Q, Nrm)
+    for variant in ("p2p_welsch", "p2pl_welsch"):
+        got = fr.target_nu_min(t, variant, 1.0)
+        ref = oracle.nu_min_point_to_point(Q.astype(float)) if variant == "p2p_welsch" else \
+            oracle.nu_min_point_to_plane(Q.astype(float), Nrm.astype(float))
+        assert got == pytest.approx(ref, rel=1e-12, abs=1e-300)
+    t.destroy()
+
+
+def test_nu_min_workload3_target_sample(fr):
+    pair = synth.config_pair(3, 0.02)                  # N = 10000 on the ellipsoids, analytic normals
+    nz = oracle.normalization(pair.P.astype(float), pair.Q.astype(float))
+    t = fr.target_create(pair.Q, pair.normals)
+    Qn = nz.fwd(pair.Q.astype(float))
+    assert fr.target_nu_min(t, "p2pl_welsch", nz.s) == pytest.approx(
+        oracle.nu_min_point_to_plane(Qn, pair.normals.astype(float)), rel=1e-9)
+    assert fr.target_nu_min(t, "p2p_welsch", nz.s) == pytest.approx(oracle.nu_min_point_to_point(Qn), rel=1e-9)
+    t.destroy()
+
+
 # --------------------------------------------------------------------------
 # Whole registrations
 # --------------------------------------------------------------------------
