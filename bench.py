@@ -17,6 +17,18 @@ iteration until the last nu stage converges. Metric = M x iterations / time.
 N > 1 runs independent replicas, one per rank (weak scaling), launched by
 torch.distributed.run. --impl reference times the FP64 CPU oracle on a bounded
 sample of the same workload instead.
+
+Two more workloads, each printing its own line next to the plain
+one-registration-at-a-time GPU path on the same inputs (rank 0 only):
+  --workload batched  256 independent pairs (M, N log-uniform in [2k, 200k],
+                      variants in equal thirds, torus / height field /
+                      ellipsoids, overlap U[0.5, 1], outliers U[0, 0.1]); one
+                      step = 256 target builds + one fricp_batch_register;
+  --workload serve    Poisson arrivals of robust requests (M, N log-uniform in
+                      [1k, 1M]) at {0.25, 0.5, 0.75, 0.9, 1.1} x the plain
+                      path's measured capacity, through fricp_server_* and
+                      through the plain path; regs/s and p50 / p99 latency
+                      (arrival to result) per rate.
 """
 from __future__ import annotations
 
@@ -52,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate (serve)")
     return ap.parse_args()
 
 
@@ -336,10 +350,220 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# Many-pair workloads: batched and served, each against the plain path
+# --------------------------------------------------------------------------
+
+def generate(specs):
+    """Build the pairs of `specs` on a spawn process pool (before any CUDA call)."""
+    import multiprocessing as mp
+
+    from paper_2007_07627_gb300 import synth
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, min(len(specs), os.cpu_count() or 4))) as pool:
+        return pool.map(synth.make_pair, specs, chunksize=1)
+
+
+def same_result(a, b) -> bool:
+    import numpy as np
+    return (a["iterations"] == b["iterations"] and a["corr_passes"] == b["corr_passes"]
+            and np.array_equal(a["R"], b["R"]) and np.array_equal(a["t"], b["t"]))
+
+
+def to_device(pairs):
+    import torch
+    out = []
+    for v, p in pairs:
+        out.append((v, torch.from_numpy(p.P).cuda(), torch.from_numpy(p.Q).cuda(),
+                    torch.from_numpy(p.normals).cuda() if v == "p2pl_welsch" else None))
+    torch.cuda.synchronize()
+    return out
+
+
+def run_batched(args):
+    from paper_2007_07627_gb300 import synth
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    specs = synth.batch_specs()
+    pairs = generate(specs)
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2007_07627_gb300 as fr
+    dev = to_device(pairs)
+    prms = [fr.params_default(v) for v, _ in pairs]
+    sum_m = sum(p.M for _, p in pairs)
+
+    def batched():
+        ts = [fr.target_create(q, n) for _, _, q, n in dev]
+        res = fr.batch_register(ts, [p for _, p, _, _ in dev], prms)
+        for t in ts:
+            t.destroy()
+        return res
+
+    def plain():
+        res = []
+        for (v, p, q, n), prm in zip(dev, prms):
+            t = fr.target_create(q, n)
+            res.append(fr.register(t, p, params=prm))
+            t.destroy()
+        return res
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, r
+
+    for _ in range(args.warmup):
+        batched()
+    fr.counters(reset=True)
+    clocks = ClockSampler(gpu_selector(local))
+    clocks.start()
+    bt = []
+    for _ in range(args.steps):
+        dt, rb = timed(batched)
+        bt.append(dt)
+    clk = clocks.stop()
+    launches = fr.counters(reset=True)["kernel_launches"] // args.steps
+    shape = fr.batch_last_shape()
+    pt, rp = timed(plain)
+    iters = sum(r["iterations"] for r in rb)
+    queries = sum(p.M * r["iterations"] for (_, p), r in zip(pairs, rb))
+    t_b = statistics.mean(bt)
+    line = {
+        "metric": "corr. queries/s (sum over pairs of M x iters / s); regs/s", "workload": "batched",
+        "value": queries / t_b, "unit": "queries/s", "regs_per_s": len(pairs) / t_b, "ms_per_step": 1e3 * t_b,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+        "dtype": "f64 (candidate distances f32 pairs)",
+        "config": {"workload": "256 pairs, M and N log-uniform in [2k, 200k], mixed variants and surfaces",
+                   "pairs": len(pairs), "sum_M": sum_m, "sum_N": sum(p.N for _, p in pairs),
+                   "iterations_total": iters, "step": "256 target builds + nu rules + one batched registration",
+                   "autotuned_shape": shape, "l2": "inputs 320 MB > L2"},
+        "plain": {"value": sum(p.M * r["iterations"] for (_, p), r in zip(pairs, rp)) / pt, "unit": "queries/s",
+                  "regs_per_s": len(pairs) / pt, "seconds": pt},
+        "speedup_vs_plain": pt / t_b,
+        "equal_results": sum(same_result(a, b) for a, b in zip(rb, rp)), "of": len(pairs),
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def percentile(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs), q)) if xs else None
+
+
+def run_serve(args):
+    import numpy as np
+
+    from paper_2007_07627_gb300 import synth
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    nreq = args.serve_requests
+    specs = synth.serve_specs(n=nreq)
+    reqs = generate(specs)
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2007_07627_gb300 as fr
+    dev = to_device(reqs)
+    prms = [fr.params_default(v) for v, _ in reqs]
+
+    def alone(k):
+        v, p, q, n = dev[k]
+        t = fr.target_create(q, n)
+        r = fr.register(t, p, params=prms[k])
+        t.destroy()
+        return r
+
+    alone(0)                                   # warm-up
+    service, ref = [], []
+    for k in range(nreq):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ref.append(alone(k))
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+    capacity = 1.0 / statistics.mean(service)
+    g = np.random.default_rng(synth.CONFIG_SEEDS[5])
+    rates = []
+    srv = fr.Server(max_slots=256, steps_per_sync=8)
+    for f in (0.25, 0.5, 0.75, 0.9, 1.1):
+        lam = f * capacity
+        arr = np.cumsum(g.exponential(1.0 / lam, nreq))
+        order = list(range(nreq))
+
+        # plain path: one request at a time, first come first served
+        lat_p = []
+        t0 = time.perf_counter()
+        for k in order:
+            now = time.perf_counter() - t0
+            if now < arr[k]:
+                time.sleep(arr[k] - now)
+            alone(k)
+            torch.cuda.synchronize()
+            lat_p.append(time.perf_counter() - t0 - arr[k])
+        span_p = time.perf_counter() - t0
+
+        # served path: continuous batching
+        lat_s, equal = [0.0] * nreq, 0
+        t0 = time.perf_counter()
+        nxt, live = 0, {}
+        done = 0
+        while done < nreq:
+            now = time.perf_counter() - t0
+            while nxt < nreq and arr[nxt] <= now:
+                v, p, q, n = dev[nxt]
+                t = fr.target_create(q, n)
+                live[srv.submit(t, p, prms[nxt])] = (nxt, t)
+                nxt += 1
+            if live:
+                srv.step(8)
+                for tk in list(live):
+                    r = srv.poll(tk)
+                    if r is not None:
+                        k, t = live.pop(tk)
+                        lat_s[k] = time.perf_counter() - t0 - arr[k]
+                        equal += same_result(r, ref[k])
+                        t.destroy()
+                        done += 1
+            elif nxt < nreq:
+                time.sleep(max(0.0, arr[nxt] - (time.perf_counter() - t0)))
+        span_s = time.perf_counter() - t0
+        rates.append({"rate_x_capacity": f, "arrivals_per_s": lam,
+                      "served": {"regs_per_s": nreq / span_s, "p50_s": percentile(lat_s, 50),
+                                 "p99_s": percentile(lat_s, 99)},
+                      "plain": {"regs_per_s": nreq / span_p, "p50_s": percentile(lat_p, 50),
+                                "p99_s": percentile(lat_p, 99)},
+                      "equal_results": equal, "of": nreq})
+    srv.destroy()
+    line = {
+        "metric": "served regs/s with p50/p99 latency vs plain", "workload": "serve", "unit": "regs/s",
+        "value": max(r["served"]["regs_per_s"] for r in rates), "higher_is_better": True, "n_gpus": 1,
+        "data": "synthetic", "dtype": "f64 (candidate distances f32 pairs)",
+        "config": {"workload": f"Poisson arrivals, {nreq} robust requests per rate, M and N log-uniform in "
+                               f"[1k, 1M] (mean M {statistics.mean(p.M for _, p in reqs):.0f})",
+                   "plain_capacity_regs_per_s": capacity, "plain_mean_service_s": statistics.mean(service),
+                   "request": "target build + nu rules + registration (arrival to result)"},
+        "rates": rates,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -232,7 +232,7 @@ int max_per_sm(const void *kernel) {
 // number of registrations in flight rounded to a power of two).
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, BatchShape> g_tuned;
-BatchShape g_last_shape{32, 0, 0};
+BatchShape g_last_shape{1, 0, 0};
 
 std::pair<int, int> size_class(int64_t points, int nslots) {
     int a = 0, b = 0;
@@ -257,7 +257,7 @@ class BatchEngine {
     BatchCtl *d_ctl = nullptr;
     int *h_done = nullptr;        // pinned copy of d_done
     BatchCtl *h_ctl = nullptr;    // pinned copy of d_ctl
-    BatchShape shape{32, 0, 0};
+    BatchShape shape{1, 0, 0};
     host::Graph graph;
     int graph_steps = 0;
     cudaStream_t s = nullptr;
@@ -351,13 +351,14 @@ class BatchEngine {
         return e;
     }
 
-    // Autotuner: time the search over the live registrations at their current
-    // transforms for each candidate shape and keep the fastest. The search is
-    // exact, so repeating it leaves every correspondence as it was; only the
-    // warm starts make the repeats cheaper, as in the steady state. Each
-    // candidate searches the same first quarter of the tile list (at least
-    // 64 tiles per SM where there are that many), after one full warm-up pass.
-    cudaError_t tune(int64_t points, int nslots, int total_tiles) {
+    // Autotuner: time one full search pass over the live registrations at
+    // their current transforms for each candidate shape and keep the fastest.
+    // The search is exact, so repeating it leaves every correspondence as it
+    // was; only the warm starts make the repeats cheaper, as in the steady
+    // state. Small tickets balance the warps and keep the warps in flight on a
+    // compact window of Morton-ordered queries (shared cache lines); large
+    // tickets take fewer atomics.
+    cudaError_t tune(int64_t points, int nslots) {
         const auto key = size_class(points, nslots);
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -375,23 +376,23 @@ class BatchEngine {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        const int chunks[] = {8, 16, 32, 64, 128};
-        int per_sm[3] = {nn_max, (nn_max + 1) / 2, 2};
-        BatchShape best{32, nn_max, acc_max};
+        const int chunks[] = {1, 2, 4, 8, 16};
+        int per_sm[2] = {nn_max, (nn_max + 1) / 2};
+        BatchShape best{1, nn_max, acc_max};
         float best_ms = 1e30f;
         cudaError_t e = cudaSuccess;
         // warm-up pass: sets the correspondences the timed repeats start from
         k_nn_batch<<<sm_count() * nn_max, kBlock, 0, s>>>(d_slots, d_heads, d_tile_slot, d_tile_local, d_ctl, 32,
                                                           0xffffffffu);
         counters().launches += 1;
-        const int tiles = std::min(total_tiles, std::max(total_tiles / 4, 64 * sm_count()));
         for (int c : chunks) {
-            for (int ps : per_sm) {
-                if (ps < 1 || ps > nn_max) continue;
+            for (int pi = 0; pi < 2; ++pi) {
+                const int ps = per_sm[pi];
+                if (ps < 1 || ps > nn_max || (pi == 1 && ps == per_sm[0])) continue;
                 k_reset_nn_ticket<<<1, 1, 0, s>>>(d_ctl);
                 cudaEventRecord(e0, s);
                 k_nn_batch<<<sm_count() * ps, kBlock, 0, s>>>(d_slots, d_heads, d_tile_slot, d_tile_local, d_ctl, c,
-                                                              (unsigned)tiles * (unsigned)(kBlock / c));
+                                                              0xffffffffu);
                 cudaEventRecord(e1, s);
                 counters().launches += 2;
                 e = cudaEventSynchronize(e1);
@@ -568,7 +569,7 @@ extern "C" fricp_status fricp_batch_register(int32_t npairs, const fricp_target 
         counters().h2d += sizeof(PairState);
         if (e != cudaSuccess) return cuda_fail(e, "uploading a registration");
     }
-    cudaError_t e = eng.tune(total_points, npairs, (int)total_tiles);
+    cudaError_t e = eng.tune(total_points, npairs);
     if (e != cudaSuccess) return cuda_fail(e, "tuning the batched step");
     const int chunk = ctl_prm.use_graph ? ctl_prm.steps_per_sync : 1;
     e = eng.capture(chunk);
@@ -865,13 +866,9 @@ extern "C" fricp_status fricp_server_step(fricp_server *sv, int32_t nsteps, int3
         if (st != FRICP_OK) return st;
         if (admitted > 0) {
             int64_t pts = 0;
-            int tiles = 0;
             for (const auto &r : sv->slots)
-                if (r) {
-                    pts += r->req.m;
-                    tiles += (int)((r->req.m + fricp::kBlock - 1) / fricp::kBlock);
-                }
-            cudaError_t e = sv->eng.tune(pts, count_in_flight(sv), tiles);
+                if (r) pts += r->req.m;
+            cudaError_t e = sv->eng.tune(pts, count_in_flight(sv));
             if (e == cudaSuccess) e = sv->eng.capture(sv->steps_per_graph);
             if (e != cudaSuccess) return cuda_fail(e, "tuning the served step");
             sv->tuned = true;

@@ -21,8 +21,8 @@ from scipy.spatial.transform import Rotation
 
 __all__ = [
     "Pair", "rng", "random_rigid", "torus_pair", "height_field_pair",
-    "ellipsoid_pair", "config_pair", "CONFIG_SEEDS", "BATCH_VARIANTS", "batch_pairs",
-    "serve_requests",
+    "ellipsoid_pair", "config_pair", "CONFIG_SEEDS", "BATCH_VARIANTS", "batch_specs", "make_pair",
+    "batch_pairs", "serve_specs", "serve_requests",
 ]
 
 # Seed of workload i (1-based) is 20070762 + i.
@@ -255,14 +255,13 @@ def _log_uniform(g, lo, hi) -> float:
     return math.exp(g.uniform(math.log(lo), math.log(hi)))
 
 
-def batch_pairs(seed: int = CONFIG_SEEDS[4], npairs: int = 256, lo: int = 2000, hi: int = 200_000,
+def batch_specs(seed: int = CONFIG_SEEDS[4], npairs: int = 256, lo: int = 2000, hi: int = 200_000,
                 variants=BATCH_VARIANTS) -> list:
-    """Mixed batch of independent registrations: M and N each log-uniform in
-    [lo, hi], variants cycled in equal shares, surface generator uniform over
-    torus / height field / ellipsoids, overlap U[0.5, 1], outliers U[0, 0.1],
-    rotation angle up to 30 degrees; each pair has its own sub-seed (the crop
-    planes come from a sample of max(20000, M + N) surface points).
-    Returns a list of (variant, Pair)."""
+    """Per-pair recipe of a mixed batch (cheap; make_pair builds one pair):
+    M and N each log-uniform in [lo, hi], variants cycled in equal shares,
+    surface generator uniform over torus / height field / ellipsoids, overlap
+    U[0.5, 1], outliers U[0, 0.1], rotation angle up to 30 degrees, and a
+    sub-seed per pair."""
     g = rng(seed)
     out = []
     for k in range(npairs):
@@ -272,16 +271,38 @@ def batch_pairs(seed: int = CONFIG_SEEDS[4], npairs: int = 256, lo: int = 2000, 
         overlap = float(g.uniform(0.5, 1.0))
         outliers = float(g.uniform(0.0, 0.1))
         sub_seed = int(g.integers(1 << 62))
-        pair = _GENERATORS[kind](sub_seed, M=M, N=N, overlap=overlap, outliers=outliers, max_angle=30.0,
-                                 crop_pool=max(20_000, M + N))
-        out.append((variants[k % len(variants)], pair))
+        out.append(dict(variant=variants[k % len(variants)], kind=kind, M=M, N=N, overlap=overlap,
+                        outliers=outliers, seed=sub_seed))
     return out
 
 
-def serve_requests(seed: int = CONFIG_SEEDS[5], n: int = 64, lo: int = 1000, hi: int = 1_000_000) -> list:
-    """Requests of the serving workload: robust registrations (Welsch
+def make_pair(spec: dict):
+    """(variant, Pair) of one batch_specs entry (the crop planes come from a
+    sample of max(20000, M + N) surface points)."""
+    M, N = spec["M"], spec["N"]
+    pair = _GENERATORS[spec["kind"]](spec["seed"], M=M, N=N, overlap=spec["overlap"], outliers=spec["outliers"],
+                                     max_angle=30.0, crop_pool=max(20_000, M + N))
+    return spec["variant"], pair
+
+
+def batch_pairs(seed: int = CONFIG_SEEDS[4], npairs: int = 256, lo: int = 2000, hi: int = 200_000,
+                variants=BATCH_VARIANTS) -> list:
+    """Mixed batch of independent registrations (batch_specs, then make_pair
+    for each). Returns a list of (variant, Pair)."""
+    return [make_pair(s) for s in batch_specs(seed, npairs, lo, hi, variants)]
+
+
+SERVE_VARIANTS = ("p2p_welsch", "p2pl_welsch")
+
+
+def serve_specs(seed: int = CONFIG_SEEDS[5], n: int = 64, lo: int = 1000, hi: int = 1_000_000) -> list:
+    """Recipes of serving-workload requests: robust registrations (Welsch
     point-to-point and point-to-plane, alternating), M and N log-uniform in
     [lo, hi], the same surface generators, overlap U[0.5, 1], outliers
-    U[0, 0.1]. Returns a list of (variant, Pair); arrival times are drawn by
-    the caller from the rate it sweeps."""
-    return batch_pairs(seed, n, lo, hi, variants=("p2p_welsch", "p2pl_welsch"))
+    U[0, 0.1]; arrival times are drawn by the caller from the rate it sweeps."""
+    return batch_specs(seed, n, lo, hi, variants=SERVE_VARIANTS)
+
+
+def serve_requests(seed: int = CONFIG_SEEDS[5], n: int = 64, lo: int = 1000, hi: int = 1_000_000) -> list:
+    """serve_specs built into (variant, Pair) requests."""
+    return [make_pair(s) for s in serve_specs(seed, n, lo, hi)]
