@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 CPU_SAMPLE_M = 40000                # cpu_baseline sample: half the source points, full target
 CPU_SAMPLE_ITERS = 5
 REF_SAMPLE_M = 16000                # --impl reference: 20% of the source points per step
-STEP_SOURCES = ["step.cu", "fricp_internal.cuh", "solver.cuh", "linalg.cuh", "select.cuh"]
+STEP_SOURCES = ["step.cu", "step_common.cuh", "fricp_internal.cuh", "solver.cuh", "linalg.cuh", "select.cuh"]
 
 
 def parse():

@@ -63,13 +63,14 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
         if (e == cudaSuccess) e = cudaGraphInstantiate(&graph.exec, graph.g, 0);
         if (e != cudaSuccess) rs = cuda_fail(e, "capturing the step graph");
     }
+    const int64_t per_replay = use_graph && graph.g ? graph_kernel_nodes(graph.g) : 0;
     int64_t steps = 0;
     *pass_ms = 0.0;
     *search_ms = 0.0;
     while (rs == FRICP_OK) {
         if (use_graph) {
             e = cudaGraphLaunch(graph.exec, s);
-            counters().launches += chunk;
+            counters().launches += per_replay;
         } else {
             for (int k = 0; k < chunk && e == cudaSuccess; ++k) {
                 if (timing) cudaEventRecord(tev[3 * k], s);

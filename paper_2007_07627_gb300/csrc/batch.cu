@@ -260,6 +260,7 @@ class BatchEngine {
     BatchShape shape{1, 0, 0};
     host::Graph graph;
     int graph_steps = 0;
+    int64_t graph_kernels = 0;   // kernel nodes per replay
     cudaStream_t s = nullptr;
 
     ~BatchEngine() { release(); }
@@ -334,12 +335,15 @@ class BatchEngine {
         e = cudaStreamEndCapture(s, &graph.g);
         counters().launches = before;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&graph.exec, graph.g, 0);
-        if (e == cudaSuccess) graph_steps = steps;
+        if (e == cudaSuccess) {
+            graph_steps = steps;
+            graph_kernels = host::graph_kernel_nodes(graph.g);
+        }
         return e;
     }
 
     cudaError_t run_graph() {
-        counters().launches += 3 * graph_steps + 1;
+        counters().launches += graph_kernels;
         return cudaGraphLaunch(graph.exec, s);
     }
 

@@ -163,6 +163,20 @@ inline void to_caller(const double Tn[12], double s, const double c[3], double R
     }
 }
 
+// Kernel nodes of a captured graph (what one replay launches).
+inline int64_t graph_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int64_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 struct Graph {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t g = nullptr;
