@@ -28,7 +28,11 @@ one-registration-at-a-time GPU path on the same inputs (rank 0 only):
                       [1k, 1M]) at {0.25, 0.5, 0.75, 0.9, 1.1} x the plain
                       path's measured capacity, through fricp_server_* and
                       through the plain path; regs/s and p50 / p99 latency
-                      (arrival to result) per rate.
+                      (arrival to result) per rate;
+  --workload precision  workload 3 (Welsch point-to-plane, ellipsoids N = 500k,
+                      M = 200k) in the three precision modes side by side:
+                      time, queries/s and each mode's difference from the FP64
+                      reference mode.
 """
 from __future__ import annotations
 
@@ -64,7 +68,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve", "precision"])
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate (serve)")
     return ap.parse_args()
 
@@ -556,6 +560,60 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args):
+    import numpy as np
+    import torch
+
+    from paper_2007_07627_gb300 import synth
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2007_07627_gb300 as fr
+    pair = synth.config_pair(3)
+    Pd, Qd, Nd = (torch.from_numpy(x).cuda() for x in (pair.P, pair.Q, pair.normals))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    modes = {}
+    ref = None
+    for prec in ("fp64", "fp32", "fp16"):
+        prm = fr.params_default("p2pl_welsch", precision=prec)
+        for _ in range(args.warmup):
+            t = fr.target_create(Qd, Nd)
+            fr.register(t, Pd, params=prm)
+            t.destroy()
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t = fr.target_create(Qd, Nd)
+            r = fr.register(t, Pd, params=prm)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            t.destroy()
+        if ref is None:
+            ref = r
+        c = (np.trace(r["R"] @ ref["R"].T) - 1.0) / 2.0
+        ms = 1e3 * statistics.mean(times)
+        modes[prec] = {"ms_per_registration": ms, "iterations": r["iterations"], "device_steps": r["device_steps"],
+                       "queries_per_s": pair.M * r["iterations"] / (ms / 1e3),
+                       "us_per_device_step": 1e3 * ms / r["device_steps"],
+                       "vs_fp64_mode": {"rotation_rad": float(np.arccos(np.clip(c, -1.0, 1.0))),
+                                        "t_over_diag": float(np.abs(r["t"] - ref["t"]).max() / pair.diag),
+                                        "energy_rel": abs(r["final_energy"] - ref["final_energy"]) /
+                                        abs(ref["final_energy"])}}
+    line = {"metric": "corr. queries/s (M x iters/s) per precision mode", "workload": "precision",
+            "value": modes["fp64"]["queries_per_s"], "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": "welsch_p2pl_aa_ellipsoids_N500000_M200000", "N": pair.N, "M": pair.M,
+                       "step": "target index + nu rules + source prep + all iterations",
+                       "l2": "flushed between steps"},
+            "modes": modes}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -564,6 +622,8 @@ def main():
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

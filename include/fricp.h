@@ -57,6 +57,28 @@ typedef enum {
     FRICP_P2PL_WELSCH_AA = 2
 } fricp_variant;
 
+/* Arithmetic of the correspondence search and the per-point terms. The sums,
+ * the 3x3 / 6x6 solves and the Anderson least squares are FP64 in every mode.
+ *   FRICP_PREC_FP64          the reference: candidates screened in float and
+ *                            re-ranked in double-float, so the winner is the FP64
+ *                            argmin (ties to the lowest original index); residuals,
+ *                            weights and products in FP64;
+ *   FRICP_PREC_FP32          transform, distances, residuals, weights and products in
+ *                            float (ties among equal float distances to the lowest
+ *                            original index), widened to FP64 for the sums;
+ *   FRICP_PREC_FP16_STORAGE  as FP32, on target coordinates stored as 16-bit offsets
+ *                            in their bucket's bounding box (8 B per point instead of
+ *                            16; built once per target on first use); ties to the
+ *                            lowest position in bucket order.
+ * FP32 and FP16 results differ from the FP64 oracle by their rounding (closest
+ * points within float resolution, weights to ~1e-7); registrations, not passes,
+ * are what they are meant for. */
+typedef enum {
+    FRICP_PREC_FP64 = 0,
+    FRICP_PREC_FP32 = 1,
+    FRICP_PREC_FP16_STORAGE = 2
+} fricp_precision;
+
 /* Solver parameters. fricp_params_default fills the paper's defaults. */
 typedef struct {
     int32_t variant;            /* fricp_variant */
@@ -74,6 +96,8 @@ typedef struct {
     int32_t time_passes;        /* 1: bracket every step launch with CUDA events (implies use_graph = 0) */
     int32_t max_steps;          /* hard cap on device steps (correspondence passes): 100000 */
     double  timeout_s;          /* host wait limit for one registration: 600 */
+    int32_t precision;          /* fricp_precision: FRICP_PREC_FP64 */
+    int32_t pad0;
 } fricp_params;
 
 /* Result of one registration. All transforms in the caller's coordinates. */

@@ -24,6 +24,8 @@ __all__ = [
 
 P2P_AA, P2P_WELSCH_AA, P2PL_WELSCH_AA = 0, 1, 2
 VARIANTS = {"p2p": P2P_AA, "p2p_welsch": P2P_WELSCH_AA, "p2pl_welsch": P2PL_WELSCH_AA}
+PREC_FP64, PREC_FP32, PREC_FP16_STORAGE = 0, 1, 2
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp16": PREC_FP16_STORAGE}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EDEGENERATE", 6: "EUNSUPPORTED",
           7: "EBUSY"}
 
@@ -44,7 +46,7 @@ class Params(ctypes.Structure):
         ("max_line_search", ctypes.c_int32), ("eps", ctypes.c_double), ("nu_max", ctypes.c_double),
         ("nu_min", ctypes.c_double), ("nu_min_floor", ctypes.c_double), ("steps_per_sync", ctypes.c_int32),
         ("use_graph", ctypes.c_int32), ("time_passes", ctypes.c_int32), ("max_steps", ctypes.c_int32),
-        ("timeout_s", ctypes.c_double),
+        ("timeout_s", ctypes.c_double), ("precision", ctypes.c_int32), ("pad0", ctypes.c_int32),
     ]
 
 
@@ -131,6 +133,8 @@ def params_default(variant=P2P_WELSCH_AA, **overrides) -> Params:
     p = Params()
     _check(lib().fricp_params_default(int(variant), ctypes.byref(p)))
     for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
         setattr(p, k, v)
     return p
 

@@ -36,6 +36,7 @@ thread_local std::string g_err;
 fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const fricp_params &prm, cudaStream_t s,
                        PairState *st_dev, bool *leak, double *pass_ms, double *search_ms) {
     using clock = std::chrono::steady_clock;
+    const int prec = prm.precision;
     const auto deadline = clock::now() + std::chrono::duration_cast<clock::duration>(
                                              std::chrono::duration<double>(prm.timeout_s));
     int *done_h = pinned_flag();
@@ -56,7 +57,7 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
         const int64_t before = counters().launches;   // capture records launches, it does not run them
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int k = 0; k < chunk; ++k) fricp::launch_step(a, variant, ntiles, s);
+            for (int k = 0; k < chunk; ++k) fricp::launch_step(a, variant, prec, ntiles, s);
             e = cudaStreamEndCapture(s, &graph.g);
         }
         counters().launches = before;
@@ -74,7 +75,7 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
         } else {
             for (int k = 0; k < chunk && e == cudaSuccess; ++k) {
                 if (timing) cudaEventRecord(tev[3 * k], s);
-                e = fricp::launch_step(a, variant, ntiles, s, timing ? tev[3 * k + 1] : nullptr);
+                e = fricp::launch_step(a, variant, prec, ntiles, s, timing ? tev[3 * k + 1] : nullptr);
                 if (timing) cudaEventRecord(tev[3 * k + 2], s);
             }
         }
@@ -155,6 +156,7 @@ fricp_status fricp_params_default(int32_t variant, fricp_params *out) {
     out->time_passes = 0;
     out->max_steps = 100000;
     out->timeout_s = 600.0;
+    out->precision = FRICP_PREC_FP64;
     return FRICP_OK;
 }
 
@@ -195,6 +197,7 @@ fricp_status fricp_target_destroy(fricp_target *t) {
     if (t->d.pts) cudaFree(t->d.pts);
     if (t->d.nrm) cudaFree(t->d.nrm);
     if (t->d.nodes) cudaFree(t->d.nodes);
+    if (t->d.pts16) cudaFree(t->d.pts16);
     delete t;
     return FRICP_OK;
 }
@@ -366,7 +369,7 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     a.partial = partial.p;
     a.resid = nullptr;
     a.trace = nullptr;
-    if (e == cudaSuccess) e = fricp::launch_step(a, variant, ntiles, s);
+    if (e == cudaSuccess) e = fricp::launch_step(a, variant, fricp::PREC_FP64, ntiles, s);
     PairState r;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, st_dev.p, sizeof(r), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

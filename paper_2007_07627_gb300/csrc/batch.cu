@@ -166,9 +166,16 @@ __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ sl
         const int i0 = lt * kBlock + sub * chunk;
         const int i1 = min(i0 + chunk, h.M);
         const bool p2p = h.variant != FRICP_P2PL_WELSCH_AA;
-        for (int i = i0; i < i1; ++i)
-            if (!search_query(sl.ix, sl.src, sl.prev, h, i, p2p, stk) && lane == 0)
-                sl.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+        for (int i = i0; i < i1; ++i) {
+            bool ok;
+            if (h.prec == PREC_FP32)
+                ok = search_query<PREC_FP32>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
+            else if (h.prec == PREC_FP16)
+                ok = search_query<PREC_FP16>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
+            else
+                ok = search_query<PREC_FP64>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
+            if (!ok && lane == 0) sl.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+        }
     }
 }
 
@@ -190,11 +197,29 @@ __global__ void __launch_bounds__(kBlock, 2) k_accum_batch(const Slot *__restric
         const Slot sl = slots[p];
         __syncthreads();
         if (h.variant == FRICP_P2PL_WELSCH_AA) {
-            if (accum_tile<1>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles, red, &s_last))
-                finish_pass<kSumsP2PL>(h, sl.st, sl.partial, sl.ntiles, sl.resid, sl.trace, sS);
+            bool last;
+            if (h.prec == PREC_FP32)
+                last = accum_tile<1, PREC_FP32>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
+                                                red, &s_last);
+            else if (h.prec == PREC_FP16)
+                last = accum_tile<1, PREC_FP16>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
+                                                red, &s_last);
+            else
+                last = accum_tile<1, PREC_FP64>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
+                                                red, &s_last);
+            if (last) finish_pass<kSumsP2PL>(h, sl.st, sl.partial, sl.ntiles, sl.resid, sl.trace, sS);
         } else {
-            if (accum_tile<0>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles, red, &s_last))
-                finish_pass<kSumsP2P>(h, sl.st, sl.partial, sl.ntiles, sl.resid, sl.trace, sS);
+            bool last;
+            if (h.prec == PREC_FP32)
+                last = accum_tile<0, PREC_FP32>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
+                                                red, &s_last);
+            else if (h.prec == PREC_FP16)
+                last = accum_tile<0, PREC_FP16>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
+                                                red, &s_last);
+            else
+                last = accum_tile<0, PREC_FP64>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
+                                                red, &s_last);
+            if (last) finish_pass<kSumsP2P>(h, sl.st, sl.partial, sl.ntiles, sl.resid, sl.trace, sS);
         }
         __syncthreads();   // s_tile and h are rewritten next round
     }

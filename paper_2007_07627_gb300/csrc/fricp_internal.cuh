@@ -13,6 +13,7 @@
 //   partial double[T][K] per-tile reduction records (T = ceil(M / kBlock) tiles)
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,10 +39,20 @@ constexpr float kShrink = 1.0f - 4e-6f;
 // d^2 / (2 nu^2) >= kWelschCut has weight 0 and psi 1 exactly.
 constexpr double kWelschCut = 750.0;
 
+// Precision of a registration's search and per-point terms (fricp_params.precision):
+//   PREC_FP64  candidates screened in float and re-ranked in double-float: the FP64
+//              argmin, ties to the lowest original index; per-point terms in FP64;
+//   PREC_FP32  transform, distances and weights in float (ties to the lowest
+//              original index among equal float distances); sums and solve in FP64;
+//   PREC_FP16  as PREC_FP32 on target coordinates stored as 16-bit offsets in their
+//              bucket's box (8 B per point); ties to the lowest bucket-order position.
+enum Prec : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_FP16 = 2 };
+
 struct Index {
     const float4 *pts;
     const float4 *nrm;
     const float4 *nodes;
+    const ushort4 *pts16;   // FP16 storage (x, y, z as half offsets in the bucket box), or null
     int n;
     int L;
 };
@@ -69,6 +80,7 @@ struct PairState {
     int ntiles;
     int trace_cap;
     int nu_max_given;
+    int prec;          // Prec
     double eps;
     double nu_max;
     double nu_min;
@@ -241,11 +253,33 @@ __device__ __forceinline__ void nn_init(NNLane &q, const float xh[3], const floa
 }
 
 // Make candidate p (sorted index j) the current winner unconditionally (warm start).
+template <int PREC = PREC_FP64>
 __device__ __forceinline__ void nn_seed(NNLane &q, float4 p, int j) {
     q.bestf = cand_d2f(q, p);
-    cand_d2_df(q, p, q.best_hi, q.best_lo);
+    if (PREC == PREC_FP64) {
+        cand_d2_df(q, p, q.best_hi, q.best_lo);
+    } else {
+        q.best_hi = q.bestf;
+        q.best_lo = 0.0f;
+    }
     q.best_j = j;
     q.best_orig = __float_as_int(p.w);
+}
+
+// Target point j as the search and the per-point terms see it at precision PREC
+// (.w: the tie-break key: original index, or the bucket-order position for FP16).
+template <int PREC>
+__device__ __forceinline__ float4 target_point(const Index &ix, int j) {
+    if (PREC != PREC_FP16) return __ldg(ix.pts + j);
+    const ushort4 h = __ldg(ix.pts16 + j);
+    const int leaf = ix.L + j / kLeaf;
+    const float4 lo = __ldg(ix.nodes + 2 * leaf), hi = __ldg(ix.nodes + 2 * leaf + 1);
+    float4 r;
+    r.x = fmaf(__half2float(__ushort_as_half(h.x)), hi.x - lo.x, lo.x);
+    r.y = fmaf(__half2float(__ushort_as_half(h.y)), hi.y - lo.y, lo.y);
+    r.z = fmaf(__half2float(__ushort_as_half(h.z)), hi.z - lo.z, lo.z);
+    r.w = __int_as_float(j);
+    return r;
 }
 
 // (double-float d^2, original index) lexicographic order; both pairs are
@@ -255,11 +289,12 @@ __device__ __forceinline__ bool lex_less(float ha, float la, int oa, float hb, f
 }
 
 // Returns true when p entered the tie window (the lane's bound or winner may change).
+template <int PREC = PREC_FP64>
 __device__ __forceinline__ bool nn_offer(NNLane &q, float4 p, int j) {
     const float d = cand_d2f(q, p);
     if (d <= q.bestf * kTieWindow) {
-        float hi, lo;
-        cand_d2_df(q, p, hi, lo);
+        float hi = d, lo = 0.0f;
+        if (PREC == PREC_FP64) cand_d2_df(q, p, hi, lo);
         const int o = __float_as_int(p.w);
         if (lex_less(hi, lo, o, q.best_hi, q.best_lo, q.best_orig)) {
             q.best_hi = hi;
@@ -379,6 +414,7 @@ __device__ __forceinline__ void warp_best(NNLane &q) {
 }
 
 // Returns false if the stack would overflow (the caller flags it as an error).
+template <int PREC>
 __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, int start_leaf) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -469,7 +505,7 @@ __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, in
             const int na = __shfl_sync(FULL, node, la), nb = __shfl_sync(FULL, node, lb);
             if (lane < 16 || two) {
                 const int j = ((lane < 16 ? na : nb) - ix.L) * kLeaf + (lane & 15);
-                if (j < ix.n) changed |= nn_offer(q, __ldg(ix.pts + j), j);
+                if (j < ix.n) changed |= nn_offer<PREC>(q, target_point<PREC>(ix, j), j);
             }
         }
         if (__ballot_sync(FULL, changed)) warp_best(q);   // only when some lane's bound moved
@@ -488,6 +524,7 @@ struct TargetDev {
     float4 *pts;
     float4 *nrm;
     float4 *nodes;
+    ushort4 *pts16;   // FP16 storage, built on first use (build_fp16_storage)
     double centroid[3];
     float lo[3], hi[3];
     // nu_min statistics in caller units (median over q of the median 6-NN distance,
@@ -495,7 +532,7 @@ struct TargetDev {
     double E_Q, H_Q;
 };
 
-inline Index make_index(const TargetDev &t) { return Index{t.pts, t.nrm, t.nodes, (int)t.n, t.L}; }
+inline Index make_index(const TargetDev &t) { return Index{t.pts, t.nrm, t.nodes, t.pts16, (int)t.n, t.L}; }
 
 // Per-thread accounting behind fricp_counters (defined in api.cu).
 struct Counters {
@@ -511,13 +548,15 @@ void set_last_error(const char *msg);
 cudaError_t build_target(const float *q_dev, const float *n_dev, int64_t n, cudaStream_t s,
                          TargetDev *t, int *bad_input);
 cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s);
+cudaError_t build_fp16_storage(TargetDev *t, cudaStream_t s);
 cudaError_t prepare_source(const float *p_dev, int64_t m, cudaStream_t s, float4 *src_out,
                            float lo[3], float hi[3], int *bad_input);
 cudaError_t launch_closest(const TargetDev *t, const float *p_dev, int64_t m, const double T[12],
                            int64_t *idx, double *d2, cudaStream_t s);
 // One device step: the closest-point search kernel, then the accumulate/solve
 // kernel. When `mid` is given it is recorded between the two.
-cudaError_t launch_step(const StepArgs &a, int variant, int ntiles, cudaStream_t s, cudaEvent_t mid = nullptr);
+cudaError_t launch_step(const StepArgs &a, int variant, int prec, int ntiles, cudaStream_t s,
+                        cudaEvent_t mid = nullptr);
 cudaError_t launch_setup_eval_xi(PairState *st, const double *T_normalized12, cudaStream_t s);
 
 }  // namespace fricp

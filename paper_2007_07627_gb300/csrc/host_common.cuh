@@ -73,6 +73,8 @@ inline fricp_status check_params(const fricp_params *p) {
     if (!(p->nu_min_floor > 0.0)) return fail(FRICP_EINVAL, "nu_min_floor must be > 0");
     if (p->steps_per_sync < 1 || p->steps_per_sync > 4096) return fail(FRICP_EINVAL, "steps_per_sync in 1..4096");
     if (p->max_steps < 1) return fail(FRICP_EINVAL, "max_steps must be >= 1");
+    if (p->precision < FRICP_PREC_FP64 || p->precision > FRICP_PREC_FP16_STORAGE)
+        return fail(FRICP_EINVAL, "unknown precision");
     if (!(p->timeout_s > 0.0)) return fail(FRICP_EINVAL, "timeout_s must be > 0");
     return FRICP_OK;
 }
@@ -206,6 +208,7 @@ inline PairState initial_state(const fricp_params &prm, int64_t m, int ntiles, d
     h.s = s;
     for (int a = 0; a < 3; ++a) h.c[a] = c[a];
     h.nu_max_given = prm.nu_max > 0.0;
+    h.prec = prm.precision;
     h.nu_max = prm.nu_max > 0.0 ? prm.nu_max : 0.0;
     h.nu_min = nu_min;
     h.E_prev = INFINITY;
@@ -223,6 +226,10 @@ inline fricp_status setup_pair(const TargetDev &t, const fricp_params &prm, int6
                                const float phi[3], const double *T0, int trace_cap, cudaStream_t s, PairState *h,
                                double *scale, double c[3]) {
     normalisation(t, plo, phi, scale, c);
+    if (prm.precision == FRICP_PREC_FP16_STORAGE && t.pts16 == nullptr) {
+        const cudaError_t e = build_fp16_storage(const_cast<TargetDev *>(&t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "FP16 target storage");
+    }
     const bool robust = prm.variant != FRICP_P2P_AA;
     double nu_min = 1.0;
     if (robust) {

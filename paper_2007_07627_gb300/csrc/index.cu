@@ -526,6 +526,41 @@ cudaError_t build_target(const float *q_dev, const float *n_dev, int64_t n, cuda
     return cudaSuccess;
 }
 
+// FP16 storage of the target: each point as half-precision offsets in
+// [0, 1] of its bucket's bounding box (a degenerate box axis stores 0), so a
+// decoded point lo + u (hi - lo) stays inside the box the tree tests.
+__global__ void k_encode16(const float4 *__restrict__ pts, const float4 *__restrict__ nodes, int n, int L,
+                           ushort4 *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float4 p = pts[j];
+    const int leaf = L + j / kLeaf;
+    const float4 lo = nodes[2 * leaf], hi = nodes[2 * leaf + 1];
+    const float ex = hi.x - lo.x, ey = hi.y - lo.y, ez = hi.z - lo.z;
+    const float ux = ex > 0.0f ? fminf(fmaxf((p.x - lo.x) / ex, 0.0f), 1.0f) : 0.0f;
+    const float uy = ey > 0.0f ? fminf(fmaxf((p.y - lo.y) / ey, 0.0f), 1.0f) : 0.0f;
+    const float uz = ez > 0.0f ? fminf(fmaxf((p.z - lo.z) / ez, 0.0f), 1.0f) : 0.0f;
+    out[j] = make_ushort4(__half_as_ushort(__float2half_rn(ux)), __half_as_ushort(__float2half_rn(uy)),
+                          __half_as_ushort(__float2half_rn(uz)), 0);
+}
+
+cudaError_t build_fp16_storage(TargetDev *t, cudaStream_t s) {
+    if (t->pts16) return cudaSuccess;
+    ushort4 *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(ushort4) * (size_t)t->n);
+    if (e != cudaSuccess) return e;
+    k_encode16<<<(unsigned)((t->n + 255) / 256), 256, 0, s>>>(t->pts, t->nodes, (int)t->n, t->L, p);
+    counters().launches += 1;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return e;
+    }
+    t->pts16 = p;
+    return cudaSuccess;
+}
+
 cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
     if (t->E_Q >= 0.0 && (!t->has_normals || t->H_Q >= 0.0)) return cudaSuccess;
     if (t->n < 7) {   // fewer than six neighbours: statistic undefined, use 0 (clamped later)

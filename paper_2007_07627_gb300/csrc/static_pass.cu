@@ -139,7 +139,7 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
     a.partial = partial;
     a.resid = nullptr;
     a.trace = nullptr;
-    if (e == cudaSuccess) e = fricp::launch_step(a, variant, ntiles, s);
+    if (e == cudaSuccess) e = fricp::launch_step(a, variant, fricp::PREC_FP64, ntiles, s);
     PairState r;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, st_dev, sizeof(r), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -18,7 +18,7 @@ namespace {
 // Search kernel: persistent warps walk the Morton-ordered queries; each query
 // is searched by a whole warp. Writes prev[i] = this pass's correspondence (the
 // next pass's warm start).
-template <int VAR>
+template <int PREC>
 __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
     __shared__ StepHead h;
     __shared__ int s_stk[kBlock / 32][kWarpStack];
@@ -28,14 +28,15 @@ __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
     const int wpb = kBlock / 32;
     int *stk = s_stk[threadIdx.x >> 5];
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < h.M; i += gridDim.x * wpb) {
-        if (!search_query(a.ix, a.src, a.prev, h, i, VAR == 0, stk) && (threadIdx.x & 31) == 0)
+        if (!search_query<PREC>(a.ix, a.src, a.prev, h, i, h.variant != FRICP_P2PL_WELSCH_AA, stk) &&
+            (threadIdx.x & 31) == 0)
             a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
     }
 }
 
 // Accumulate kernel: one tile of points per block; the block that completes
 // the pass reduces the records and runs the solver step.
-template <int VAR>
+template <int VAR, int PREC>
 __global__ void __launch_bounds__(kBlock) k_accum(StepArgs a) {
     constexpr int K = VAR ? kSumsP2PL : kSumsP2P;
     __shared__ StepHead h;
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(kBlock) k_accum(StepArgs a) {
     if (threadIdx.x == 0) load_head(a.st, h);
     __syncthreads();
     if (h.done) return;
-    if (accum_tile<VAR>(h, a.st, a.ix, a.src, a.prev, a.resid, a.partial, blockIdx.x, gridDim.x, red, &s_last))
+    if (accum_tile<VAR, PREC>(h, a.st, a.ix, a.src, a.prev, a.resid, a.partial, blockIdx.x, gridDim.x, red, &s_last))
         finish_pass<K>(h, a.st, a.partial, gridDim.x, a.resid, a.trace, sS);
 }
 
@@ -91,31 +92,39 @@ __global__ void k_setup_eval(PairState *st, const double *T) {
 
 }  // namespace
 
-// Blocks of the search kernel (persistent warps): enough to fill every SM.
+// Blocks of the search kernel k_nn<PREC> (persistent warps): enough to fill
+// every SM at that kernel's occupancy, and no more than the queries need.
+template <int PREC>
 int nn_blocks(int M) {
     static int nb = 0;
     if (nb == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nn<0>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nn<PREC>, kBlock, 0);
         nb = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
     }
     const int need = (M + kBlock / 32 - 1) / (kBlock / 32);
     return need < nb ? need : nb;
 }
 
-cudaError_t launch_step(const StepArgs &a, int variant, int ntiles, cudaStream_t s, cudaEvent_t mid) {
-    const int nb = nn_blocks(ntiles * kBlock);
-    if (variant == FRICP_P2PL_WELSCH_AA) {
-        k_nn<1><<<nb, kBlock, 0, s>>>(a);
-        if (mid) cudaEventRecord(mid, s);
-        k_accum<1><<<ntiles, kBlock, 0, s>>>(a);
-    } else {
-        k_nn<0><<<nb, kBlock, 0, s>>>(a);
-        if (mid) cudaEventRecord(mid, s);
-        k_accum<0><<<ntiles, kBlock, 0, s>>>(a);
-    }
+template <int PREC>
+void launch_step_prec(const StepArgs &a, int variant, int ntiles, cudaStream_t s, cudaEvent_t mid) {
+    k_nn<PREC><<<nn_blocks<PREC>(ntiles * kBlock), kBlock, 0, s>>>(a);
+    if (mid) cudaEventRecord(mid, s);
+    if (variant == FRICP_P2PL_WELSCH_AA)
+        k_accum<1, PREC><<<ntiles, kBlock, 0, s>>>(a);
+    else
+        k_accum<0, PREC><<<ntiles, kBlock, 0, s>>>(a);
+}
+
+cudaError_t launch_step(const StepArgs &a, int variant, int prec, int ntiles, cudaStream_t s, cudaEvent_t mid) {
+    if (prec == PREC_FP32)
+        launch_step_prec<PREC_FP32>(a, variant, ntiles, s, mid);
+    else if (prec == PREC_FP16)
+        launch_step_prec<PREC_FP16>(a, variant, ntiles, s, mid);
+    else
+        launch_step_prec<PREC_FP64>(a, variant, ntiles, s, mid);
     counters().launches += 2;
     return cudaGetLastError();
 }

@@ -66,13 +66,14 @@ struct StepHead {
     double scale, inv2nu2;
     float Rh[9], Rl[9], th[3], tl[3];   // float splits of R and t for the search
     float cut2;
-    int phase, done, welsch, M, variant;
+    int phase, done, welsch, M, variant, prec;
 };
 
 __device__ __forceinline__ void load_head(const PairState *st, StepHead &h) {
     h.done = st->done;
     h.phase = st->phase;
     h.variant = st->variant;
+    h.prec = st->prec;
     h.welsch = st->variant != FRICP_P2P_AA;
     h.M = st->M;
     for (int i = 0; i < 9; ++i) h.R[i] = st->Re[i];
@@ -100,42 +101,110 @@ __device__ __forceinline__ void transform_point(const StepHead &h, float4 p, dou
 // weight cap: a point farther than the cap has weight exp(-a) = 0.0 and
 // psi = 1.0 exactly for every candidate that far, so the search radius is capped
 // there (the sums are bit-identical).
+template <int PREC>
 __device__ __forceinline__ void start_query(const Index &ix, const float4 *src, const int *prev, const StepHead &h,
                                             int i, bool p2p, NNLane &q) {
     float xh[3], xl[3];
-    df_transform(h.Rh, h.Rl, h.th, h.tl, __ldg(src + i), xh, xl);
+    const float4 p = __ldg(src + i);
+    if (PREC == PREC_FP64) {
+        df_transform(h.Rh, h.Rl, h.th, h.tl, p, xh, xl);
+    } else {   // float transform with R and t rounded to float
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            xh[r] = fmaf(h.Rh[3 * r], p.x, fmaf(h.Rh[3 * r + 1], p.y, fmaf(h.Rh[3 * r + 2], p.z, h.th[r])));
+            xl[r] = 0.0f;
+        }
+    }
     nn_init(q, xh, xl);
     const int j0 = prev[i];
-    if (j0 >= 0) nn_seed(q, __ldg(ix.pts + j0), j0);
+    if (j0 >= 0) nn_seed<PREC>(q, target_point<PREC>(ix, j0), j0);
     if (p2p && h.welsch && h.phase != PH_INIT && h.cut2 < q.bestf) q.bestf = h.cut2;
 }
 
 // One query searched by the whole warp; lane 0 stores the correspondence (the
 // next pass's warm start). Returns false on a search-stack overflow.
+template <int PREC>
 __device__ __forceinline__ bool search_query(const Index &ix, const float4 *src, int *prev, const StepHead &h, int i,
                                              bool p2p, int *stk) {
     NNLane q;   // every lane sets up the same query (float arithmetic, broadcast loads)
-    start_query(ix, src, prev, h, i, p2p, q);
-    const bool ok = warp_nn(ix, q, stk, q.best_j >= 0 ? q.best_j / kLeaf : -1);
+    start_query<PREC>(ix, src, prev, h, i, p2p, q);
+    const bool ok = warp_nn<PREC>(ix, q, stk, q.best_j >= 0 ? q.best_j / kLeaf : -1);
     if (!ok) q.best_j = 0;
     if ((threadIdx.x & 31) == 0) prev[i] = q.best_j < 0 ? 0 : q.best_j;   // -1 only if nothing lies inside the cap
     __syncwarp();
     return ok;
 }
 
-// Point i's share of the pass sums at this pass's correspondence (FP64):
+// Point i's share of the pass sums at this pass's correspondence:
 // Welsch weight and energy term (Eq. 10, Eq. 12, Eq. 16); point-to-point: the
 // weighted centroids and cross-covariance terms; point-to-plane: g z z^T, g z h
 // and the energy with z = [y x n; n] (App. D). At PH_INIT the residual is kept
-// for the nu_max median.
-template <int VAR>
+// for the nu_max median. PREC_FP64: every term in FP64. PREC_FP32 / PREC_FP16:
+// transform, residual, weight and the products in float, widened to FP64 for
+// the sums.
+template <int VAR, int PREC>
 __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, const float4 *src, const int *prev,
                                             double *resid, int i, double (&acc)[VAR ? kSumsP2PL : kSumsP2P]) {
     const float4 p = __ldg(src + i);
+    const int j = prev[i];
+    const float4 q = target_point<PREC>(ix, j);
+    if (PREC != PREC_FP64) {
+        float x[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            x[r] = fmaf(h.Rh[3 * r], p.x, fmaf(h.Rh[3 * r + 1], p.y, fmaf(h.Rh[3 * r + 2], p.z, h.th[r])));
+        const float dx = x[0] - q.x, dy = x[1] - q.y, dz = x[2] - q.z;
+        const float s = (float)h.scale, c0 = (float)h.c[0], c1 = (float)h.c[1], c2 = (float)h.c[2];
+        const float i2 = (float)h.inv2nu2;
+        const float pt[3] = {p.x - c0, p.y - c1, p.z - c2};
+        if (VAR == 0) {
+            const float d2n = s * s * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            float w, psi;
+            if (h.welsch) {
+                w = expf(-d2n * i2);
+                psi = 1.0f - w;
+            } else {
+                w = 1.0f;
+                psi = d2n;
+            }
+            if (h.phase == PH_INIT) resid[i] = (double)sqrtf(d2n);
+            const float qt[3] = {q.x - c0, q.y - c1, q.z - c2};
+            acc[0] = w;
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                acc[1 + u] = (double)(w * pt[u]);
+                acc[4 + u] = (double)(w * qt[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) acc[7 + 3 * u + v] = (double)(w * pt[u] * qt[v]);
+            acc[16] = psi;
+        } else {
+            const float4 nv = __ldg(ix.nrm + j);
+            const float hh = s * fmaf(dz, nv.z, fmaf(dy, nv.y, dx * nv.x));
+            if (h.phase == PH_INIT) resid[i] = (double)fabsf(hh);
+            const float g = expf(-hh * hh * i2);
+            float y[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                y[r] = s * fmaf(h.Rh[3 * r], pt[0], fmaf(h.Rh[3 * r + 1], pt[1], h.Rh[3 * r + 2] * pt[2]));
+            const float z[6] = {y[1] * nv.z - y[2] * nv.y, y[2] * nv.x - y[0] * nv.z, y[0] * nv.y - y[1] * nv.x,
+                                nv.x, nv.y, nv.z};
+            int t = 0;
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                const float gz = g * z[r];
+#pragma unroll
+                for (int c = r; c < 6; ++c) acc[t++] = (double)(gz * z[c]);
+                acc[21 + r] = (double)(gz * hh);
+            }
+            acc[27] = (double)(1.0f - g);
+        }
+        return;
+    }
     double x[3];
     transform_point(h, p, x);
-    const int j = prev[i];
-    const float4 q = __ldg(ix.pts + j);
     const double dx = x[0] - (double)q.x, dy = x[1] - (double)q.y, dz = x[2] - (double)q.z;
     const double s = h.scale;
     const double pt[3] = {(double)p.x - h.c[0], (double)p.y - h.c[1], (double)p.z - h.c[2]};
@@ -188,7 +257,7 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
 // One tile of kBlock points of a registration: per-point terms, then the tile's
 // FP64 record at partial[tile * K]. Returns true in every thread of the block
 // that completed the registration's pass (the last of its tiles to finish).
-template <int VAR>
+template <int VAR, int PREC>
 __device__ __forceinline__ bool accum_tile(const StepHead &h, PairState *st, const Index &ix, const float4 *src,
                                            const int *prev, double *resid, double *partial, int tile, int ntiles,
                                            double *red, int *s_last) {
@@ -197,7 +266,7 @@ __device__ __forceinline__ bool accum_tile(const StepHead &h, PairState *st, con
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
     const int i = tile * kBlock + threadIdx.x;
-    if (i < h.M) accum_point<VAR>(h, ix, src, prev, resid, i, acc);
+    if (i < h.M) accum_point<VAR, PREC>(h, ix, src, prev, resid, i, acc);
     block_reduce_store<K>(acc, partial + (size_t)tile * K, red);
     __threadfence();
     __syncthreads();
