@@ -407,3 +407,61 @@ def test_solve_jitter_is_off_by_default_and_small_on_a_well_posed_case(variant):
     c = oracle.register(P, Q, dataclasses.replace(prm, solve_jitter=1e-13, jitter_seed=5), normals=N)
     assert np.abs(c["R"] - a["R"]).max() < 1e-10
     assert np.abs(c["t"] - a["t"]).max() < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Normal estimate (Sec. 6: PCA over the k nearest neighbours)
+# --------------------------------------------------------------------------
+
+def test_knn_all_includes_self_and_orders_by_distance_then_index():
+    g = np.random.default_rng(31)
+    Q = g.random((400, 3))
+    Q[300:310] = Q[5]                                  # duplicates at distance 0
+    idx, d2 = oracle.knn_all(Q, 12)
+    D = ((Q[:, None, :] - Q[None, :, :]) ** 2).sum(-1)
+    for i in range(0, 400, 7):
+        order = np.lexsort((np.arange(400), D[i]))[:12]
+        assert list(idx[i]) == list(order)
+        assert np.array_equal(d2[i], D[i][order])
+    assert idx[5, 0] == 5 and set(idx[5, 1:11]) == set(range(300, 310))
+
+
+def test_normals_of_a_plane_are_its_normal():
+    g = np.random.default_rng(32)
+    a, b, c = 0.3, -0.7, 0.2
+    xy = g.random((3000, 2))
+    Q = np.column_stack([xy, a * xy[:, 0] + b * xy[:, 1] + c])
+    n_true = np.array([-a, -b, 1.0]) / np.linalg.norm([-a, -b, 1.0])
+    v = np.array([0.5, 0.5, 5.0])                      # above the plane
+    N = oracle.estimate_normals(Q, 30, viewpoint=v)
+    assert np.abs(N - n_true[None, :]).max() < 1e-9
+    assert (np.einsum("nd,nd->n", N, v - Q) >= 0).all()
+
+
+def test_normals_of_a_sphere_are_radial_and_turned_to_the_viewpoint():
+    g = np.random.default_rng(33)
+    u = g.standard_normal((5000, 3))
+    Q = u / np.linalg.norm(u, axis=1, keepdims=True)
+    N = oracle.estimate_normals(Q, 30)                 # viewpoint: the origin, inside the sphere
+    cos = np.einsum("nd,nd->n", N, -Q)                 # inward
+    assert (cos > 0).all()
+    ang = np.arccos(np.clip(cos, -1, 1))
+    # neighbourhood radius about 0.15: a tilted PCA plane stays within a few degrees
+    assert ang.mean() < 0.02 and ang.max() < 0.1
+
+
+def test_normal_minimises_the_rayleigh_quotient():
+    """The normal is the direction of least spread of the neighbourhood: its
+    quotient n^T C n is below that of 20000 random unit directions."""
+    g = np.random.default_rng(34)
+    Q = g.standard_normal((200, 3)) * [1.0, 0.5, 0.1]
+    N = oracle.estimate_normals(Q, 30)
+    idx, _ = oracle.knn_all(Q, 30)
+    U = g.standard_normal((20000, 3))
+    U /= np.linalg.norm(U, axis=1, keepdims=True)
+    for i in range(0, 200, 17):
+        nb = Q[idx[i]]
+        C = (nb - nb.mean(0)).T @ (nb - nb.mean(0)) / 30
+        qn = N[i] @ C @ N[i]
+        assert qn <= np.einsum("nd,de,ne->n", U, C, U).min() + 1e-12
+        assert abs(np.linalg.norm(N[i]) - 1.0) < 1e-12
