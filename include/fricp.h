@@ -139,6 +139,20 @@ fricp_status fricp_params_default(int32_t variant, fricp_params *out);
 fricp_status fricp_target_create(const float *q_xyz, const float *q_normals, int64_t n,
                                  int32_t on_device, void *stream, fricp_target **out);
 
+/* Unit normals of a point set whose surface is unknown, as the paper
+ * estimates them for real scans (Sec. 6: from the 30 nearest neighbours;
+ * k = 30 reproduces that). The neighbourhood of q_i is its k nearest points
+ * of the set, q_i included, ordered by (FP64 squared distance, index); the
+ * normal is the unit eigenvector of the smallest eigenvalue of the
+ * neighbourhood's covariance about its centroid, turned so that
+ * n . (viewpoint - q_i) >= 0 (viewpoint: double[3], NULL = the origin).
+ * q_xyz and normals_out: float32 [n][3], both host or both device memory (per
+ * on_device). 3 <= k <= 32 (k is capped at n). The result can be passed as
+ * q_normals to fricp_target_create. Blocks until the normals are written.
+ * Errors: EINVAL (bad pointer/size/k/NaN), ENOMEM, ECUDA. */
+fricp_status fricp_estimate_normals(const float *q_xyz, int64_t n, int32_t k, int32_t on_device,
+                                    const double *viewpoint, float *normals_out, void *stream);
+
 /* Release a target (NULL is accepted). Waits for work queued on the target's
  * creation stream. */
 fricp_status fricp_target_destroy(fricp_target *target);

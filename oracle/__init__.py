@@ -96,6 +96,8 @@ def _load():
         lib.oracle_knn_self.restype = None
         lib.oracle_knn_all.argtypes = [dp, ctypes.c_int64, ctypes.c_int, ip, dp]
         lib.oracle_knn_all.restype = None
+        lib.oracle_knn_query.argtypes = [dp, ctypes.c_int64, dp, ctypes.c_int64, ctypes.c_int, ip, dp]
+        lib.oracle_knn_query.restype = None
         _lib = lib
     return _lib
 
@@ -151,22 +153,42 @@ def knn_all(Q: np.ndarray, k: int):
     return idx, d2
 
 
-def estimate_normals(Q: np.ndarray, k: int = 30, viewpoint=None) -> np.ndarray:
+def knn_query(X: np.ndarray, Q: np.ndarray, k: int):
+    """k nearest points of Q for each row of X, ascending (d^2, index of Q)."""
+    lib = _load()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    m, n = X.shape[0], Q.shape[0]
+    k = min(k, n)
+    idx = np.empty((m, k), np.int64)
+    d2 = np.empty((m, k), np.float64)
+    if m:
+        lib.oracle_knn_query(_dp(X), m, _dp(Q), n, k, _ip(idx), _dp(d2))
+    return idx, d2
+
+
+def estimate_normals(Q: np.ndarray, k: int = 30, viewpoint=None, rows=None) -> np.ndarray:
     """Normals of a point set where the surface is unknown (Sec. 6: the paper uses
     PCL's estimate over 30 nearest neighbours). Reading: the neighbourhood of q_i is
     its k nearest points in Q, q_i included, ties to the lower index; the normal
     is the unit eigenvector of the smallest eigenvalue of the neighbourhood's
     covariance (1/k) sum (q_j - c)(q_j - c)^T about its centroid c, turned so that
-    n . (viewpoint - q_i) >= 0 (viewpoint: the origin when not given)."""
+    n . (viewpoint - q_i) >= 0 (viewpoint: the origin when not given). rows: only
+    those points' normals (all when None)."""
     Q = np.asarray(Q, dtype=np.float64)
     v = np.zeros(3) if viewpoint is None else np.asarray(viewpoint, dtype=np.float64)
-    idx, _ = knn_all(Q, k)
-    nb = Q[idx]                                       # [n, k, 3]
+    if rows is None:
+        idx, _ = knn_all(Q, k)
+        at = Q
+    else:
+        at = Q[np.asarray(rows)]
+        idx, _ = knn_query(at, Q, k)
+    nb = Q[idx]                                       # [m, k, 3]
     c = nb.mean(axis=1, keepdims=True)
     C = np.einsum("nki,nkj->nij", nb - c, nb - c) / nb.shape[1]
     _, vecs = np.linalg.eigh(C)                       # ascending eigenvalues
     nrm = vecs[:, :, 0]
-    flip = np.einsum("nd,nd->n", nrm, v[None, :] - Q) < 0.0
+    flip = np.einsum("nd,nd->n", nrm, v[None, :] - at) < 0.0
     nrm[flip] *= -1.0
     return nrm
 

@@ -15,6 +15,8 @@
  *                    Sec. 5), by exhaustive search, ascending (d^2, index).
  * oracle_knn_all   : the same with q_i itself included (the neighbourhoods of
  *                    the normal estimate of Sec. 6).
+ * oracle_knn_query : the k nearest points of Q of arbitrary query points x
+ *                    (a point of Q queried at its own position finds itself).
  *
  * Compiled with -ffp-contract=off so x86-64 and AArch64 give identical bits.
  */
@@ -95,6 +97,37 @@ void oracle_knn_all(const double *q, int64_t n, int k, int64_t *idx, double *d2)
             bi[s] = -1;
         }
         const double x0 = q[3 * i], x1 = q[3 * i + 1], x2 = q[3 * i + 2];
+        for (int64_t j = 0; j < n; ++j) {
+            const double a = q[3 * j] - x0;
+            const double b = q[3 * j + 1] - x1;
+            const double c = q[3 * j + 2] - x2;
+            const double d = a * a + b * b + c * c;
+            if (!(d < bd[k - 1]))
+                continue;
+            int s = k - 1;
+            while (s > 0 && bd[s - 1] > d) {
+                bd[s] = bd[s - 1];
+                bi[s] = bi[s - 1];
+                --s;
+            }
+            bd[s] = d;
+            bi[s] = j;
+        }
+    }
+}
+
+void oracle_knn_query(const double *x, int64_t m, const double *q, int64_t n, int k, int64_t *idx, double *d2)
+{
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (i = 0; i < m; ++i) {
+        double *bd = d2 + i * k;
+        int64_t *bi = idx + i * k;
+        for (int s = 0; s < k; ++s) {
+            bd[s] = INFINITY;
+            bi[s] = -1;
+        }
+        const double x0 = x[3 * i], x1 = x[3 * i + 1], x2 = x[3 * i + 2];
         for (int64_t j = 0; j < n; ++j) {
             const double a = q[3 * j] - x0;
             const double b = q[3 * j + 1] - x1;

@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
     L.fricp_batch_register.argtypes = [i32, pp, pp, ctypes.POINTER(i64), i32, dp, ctypes.POINTER(Params), vp,
                                        ctypes.POINTER(Result), dp, i32]
     L.fricp_batch_last_shape.argtypes = [ctypes.POINTER(i32)] * 3
+    L.fricp_estimate_normals.argtypes = [vp, i64, i32, i32, dp, vp, vp]
     L.fricp_server_create.argtypes = [ctypes.c_size_t, i32, i32, i32, vp, ctypes.POINTER(vp)]
     L.fricp_server_submit.argtypes = [vp, vp, vp, i64, i32, dp, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)]
     L.fricp_server_step.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -105,7 +106,7 @@ def lib() -> ctypes.CDLL:
     for name in ("fricp_params_default", "fricp_target_create", "fricp_target_destroy", "fricp_register",
                  "fricp_closest_points", "fricp_eval_pass", "fricp_target_nu_min", "fricp_batch_register",
                  "fricp_server_create", "fricp_server_submit", "fricp_server_step", "fricp_server_poll",
-                 "fricp_server_destroy"):
+                 "fricp_server_destroy", "fricp_estimate_normals"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -280,6 +281,25 @@ def batch_last_shape() -> dict:
     c, a, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     lib().fricp_batch_last_shape(ctypes.byref(c), ctypes.byref(a), ctypes.byref(b))
     return {"chunk": c.value, "search_blocks_per_sm": a.value, "accumulate_blocks_per_sm": b.value}
+
+
+def estimate_normals(q, k: int = 30, viewpoint=None, stream=None):
+    """fricp_estimate_normals: PCA normals over the k nearest neighbours (Sec. 6).
+    Returns float32 [n, 3] in q's memory space (numpy array or CUDA tensor)."""
+    qp, n, dev, qk = _points(q)
+    if dev:
+        import torch
+        out = torch.empty((n, 3), dtype=torch.float32, device=qk.device)
+        op = ctypes.c_void_p(out.data_ptr())
+    else:
+        out = np.empty((n, 3), np.float32)
+        op = out.ctypes.data_as(ctypes.c_void_p)
+    vp = None
+    if viewpoint is not None:
+        va = np.ascontiguousarray(np.asarray(viewpoint, dtype=np.float64).reshape(3))
+        vp = va.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(lib().fricp_estimate_normals(qp, n, int(k), dev, vp, op, _stream(stream)))
+    return out
 
 
 class Server:

@@ -191,6 +191,46 @@ fricp_status fricp_target_create(const float *q_xyz, const float *q_normals, int
     return FRICP_OK;
 }
 
+fricp_status fricp_estimate_normals(const float *q_xyz, int64_t n, int32_t k, int32_t on_device,
+                                    const double *viewpoint, float *normals_out, void *stream) {
+    if (!q_xyz || !normals_out) return fail(FRICP_EINVAL, "NULL argument");
+    if (n < 1 || n > (int64_t)1 << 30) return fail(FRICP_EINVAL, "n must be in 1..2^30");
+    if (k < 3 || k > 32) return fail(FRICP_EINVAL, "k must be in 3..32");
+    double v[3] = {0.0, 0.0, 0.0};
+    if (viewpoint)
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(viewpoint[a])) return fail(FRICP_EINVAL, "viewpoint has NaN or Inf");
+            v[a] = viewpoint[a];
+        }
+    Ordered ord(stream);
+    const cudaStream_t s = ord.work;
+    DevInput q;
+    fricp_status st = stage_input(q_xyz, n, on_device, s, &q, "q_xyz");
+    if (st != FRICP_OK) return st;
+    TargetDev t;
+    std::memset(&t, 0, sizeof(t));
+    int bad = 0;
+    cudaError_t e = fricp::build_target(q.ptr, nullptr, n, s, &t, &bad);
+    DevBuf<float> out;
+    if (e == cudaSuccess && !bad && !on_device && out.alloc(3 * (size_t)n, s) != cudaSuccess)
+        e = cudaErrorMemoryAllocation;
+    int overflow = 0;
+    if (e == cudaSuccess && !bad)
+        e = fricp::estimate_normals(&t, k, v, on_device ? normals_out : out.p, s, &overflow);
+    if (e == cudaSuccess && !bad && !on_device) {
+        e = cudaMemcpyAsync(normals_out, out.p, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s);
+        counters().d2h += (int64_t)sizeof(float) * 3 * n;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (t.pts) cudaFree(t.pts);
+    if (t.nodes) cudaFree(t.nodes);
+    if (bad) return fail(FRICP_EINVAL, "q_xyz has NaN or Inf");
+    if (e == cudaErrorMemoryAllocation) return fail(FRICP_ENOMEM, "device allocation for the normal estimate");
+    if (e != cudaSuccess) return cuda_fail(e, "normal estimate");
+    if (overflow) return fail(FRICP_ECUDA, "neighbour search stack overflow");
+    return FRICP_OK;
+}
+
 fricp_status fricp_target_destroy(fricp_target *t) {
     if (t == nullptr) return FRICP_OK;
     cudaDeviceSynchronize();

@@ -548,6 +548,8 @@ void set_last_error(const char *msg);
 cudaError_t build_target(const float *q_dev, const float *n_dev, int64_t n, cudaStream_t s,
                          TargetDev *t, int *bad_input);
 cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s);
+cudaError_t estimate_normals(const TargetDev *t, int k, const double viewpoint[3], float *out_dev, cudaStream_t s,
+                             int *overflow_out);
 cudaError_t build_fp16_storage(TargetDev *t, cudaStream_t s);
 cudaError_t prepare_source(const float *p_dev, int64_t m, cudaStream_t s, float4 *src_out,
                            float lo[3], float hi[3], int *bad_input);

@@ -387,6 +387,272 @@ __global__ void __launch_bounds__(kKnnBlock) k_knn6_stats(Index ix, double *__re
     }
 }
 
+// ---------------------------------------------------------------------------
+// Normal estimate (Sec. 6: where the surface is unknown the paper estimates
+// normals from the 30 nearest neighbours): the neighbourhood of q_i is its k
+// nearest points, q_i included, ordered by (exact FP64 squared distance,
+// original index); the normal is the eigenvector of the smallest eigenvalue of
+// the neighbourhood's covariance about its centroid, turned towards a viewpoint.
+//
+// k_knn_cov: one warp per point, the traversal of warp_knn6. The warp keeps the
+// sorted k nearest one entry per lane (lane s holds the s-th nearest), inserts a
+// candidate with one ballot and one shift, and prunes in float against the k-th
+// distance rounded up. Candidate distances are FP64 without fused
+// multiply-adds, so the order is that of a plain evaluation of
+// (dx^2 + dy^2) + dz^2. Writes the 6 covariance entries per point.
+// ---------------------------------------------------------------------------
+constexpr int kMaxNormalK = 32;
+
+__device__ __forceinline__ double exact_d2(float4 q, const float xq[3]) {
+    const double a0 = (double)q.x - (double)xq[0], a1 = (double)q.y - (double)xq[1], a2 = (double)q.z - (double)xq[2];
+    return __dadd_rn(__dadd_rn(__dmul_rn(a0, a0), __dmul_rn(a1, a1)), __dmul_rn(a2, a2));
+}
+
+struct TopK {
+    double d;   // lane s: the s-th smallest squared distance so far
+    int o, j;   // its original index and bucket-order position
+    float bound;
+};
+
+__device__ __forceinline__ void topk_scan(const Index &ix, const float xq[3], TopK &t, int K, int na, int nb,
+                                          bool two) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    bool cand = false;
+    double d = 0.0;
+    int o = 0, j = -1;
+    if (lane < 16 || two) {
+        j = ((lane < 16 ? na : nb) - ix.L) * kLeaf + (lane & 15);
+        if (j < ix.n) {
+            const float4 q = __ldg(ix.pts + j);
+            const float fx = q.x - xq[0], fy = q.y - xq[1], fz = q.z - xq[2];
+            if (fmaf(fz, fz, fmaf(fy, fy, fx * fx)) * kShrink <= t.bound) {
+                d = exact_d2(q, xq);
+                o = __float_as_int(q.w);
+                cand = true;
+            }
+        }
+    }
+    unsigned cm = __ballot_sync(FULL, cand);
+    while (cm) {   // insert in lane order
+        const int src = __ffs(cm) - 1;
+        cm &= cm - 1u;
+        const double dv = __shfl_sync(FULL, d, src);
+        const int ov = __shfl_sync(FULL, o, src), jv = __shfl_sync(FULL, j, src);
+        const bool greater = lane < K && (t.d > dv || (t.d == dv && t.o > ov));
+        const unsigned gm = __ballot_sync(FULL, greater);
+        if (gm == 0u) continue;   // not among the K nearest
+        const int pos = __ffs(gm) - 1;
+        const double ud = __shfl_up_sync(FULL, t.d, 1);
+        const int uo = __shfl_up_sync(FULL, t.o, 1), uj = __shfl_up_sync(FULL, t.j, 1);
+        if (lane == pos) {
+            t.d = dv;
+            t.o = ov;
+            t.j = jv;
+        } else if (lane > pos && lane < K) {
+            t.d = ud;
+            t.o = uo;
+            t.j = uj;
+        }
+        t.bound = __double2float_ru(__shfl_sync(FULL, t.d, K - 1));
+    }
+}
+
+// Returns false if the stack would overflow.
+__device__ bool warp_knn_k(const Index &ix, int i, const float xq[3], int K, TopK &t, int *stk) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+    t.d = INFINITY;
+    t.o = 0x7fffffff;
+    t.j = -1;
+    t.bound = INFINITY;
+    int depth = 0;
+    while ((1 << depth) < ix.L) ++depth;
+    const int start = ix.L + i / kLeaf;
+    topk_scan(ix, xq, t, K, start, start ^ 1, depth > 0);   // the point's bucket and its sibling first
+    int sp;
+    {
+        int c = 0;
+        bool pass = false;
+        if (lane < depth - 1) {
+            c = (start >> (depth - 1 - lane)) ^ 1;
+            pass = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), xq, zero) * kShrink <= t.bound;
+        }
+        const unsigned m = __ballot_sync(FULL, pass);
+        if (pass) stk[__popc(m & below)] = c;
+        sp = __popc(m);
+    }
+    __syncwarp();
+    const int leaf_parent_level = depth - 1;
+    while (sp > 0) {
+        const int k = min(32, sp);
+        const int node = (lane < k) ? stk[sp - 1 - lane] : 0;
+        sp -= k;
+        __syncwarp();
+        int c[4] = {0, 0, 0, 0};
+        bool ok[4] = {false, false, false, false};
+        bool leaf_ok = false;
+        if (node != 0) {
+            if (node < ix.L) {
+                const int level = 31 - __clz(node);
+                if (level < leaf_parent_level) {
+                    const float4 *bx = ix.nodes + 8 * node;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        c[g] = 4 * node + g;
+                        ok[g] = box_d2(__ldg(bx + 2 * g), __ldg(bx + 2 * g + 1), xq, zero) * kShrink <= t.bound;
+                    }
+                } else {
+                    const float4 *bx = ix.nodes + 4 * node;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        c[g] = 2 * node + g;
+                        ok[g] = box_d2(__ldg(bx + 2 * g), __ldg(bx + 2 * g + 1), xq, zero) * kShrink <= t.bound;
+                    }
+                }
+            } else {
+                leaf_ok = box_d2(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), xq, zero) * kShrink
+                          <= t.bound;
+            }
+        }
+        int base = sp;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const unsigned mg = __ballot_sync(FULL, ok[g]);
+            if (base + __popc(mg) > kWarpStack) return false;
+            if (ok[g]) stk[base + __popc(mg & below)] = c[g];
+            base += __popc(mg);
+        }
+        sp = base;
+        unsigned lm = __ballot_sync(FULL, leaf_ok);
+        while (lm) {   // two buckets per pass: lanes 0-15 and 16-31
+            const int la = __ffs(lm) - 1;
+            lm &= lm - 1u;
+            int lb = la;
+            bool two = false;
+            if (lm) {
+                lb = __ffs(lm) - 1;
+                lm &= lm - 1u;
+                two = true;
+            }
+            const int na = __shfl_sync(FULL, node, la), nb = __shfl_sync(FULL, node, lb);
+            topk_scan(ix, xq, t, K, na, nb, two);
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kKnnBlock) k_knn_cov(Index ix, int K, double *__restrict__ cov,
+                                                       int *__restrict__ overflow) {
+    __shared__ int s_stk[kKnnBlock / 32][kWarpStack];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int wpb = kKnnBlock / 32;
+    for (int i = blockIdx.x * wpb + w; i < ix.n; i += gridDim.x * wpb) {
+        const float4 qi = __ldg(ix.pts + i);
+        const float xq[3] = {qi.x, qi.y, qi.z};
+        TopK t;
+        if (!warp_knn_k(ix, i, xq, K, t, s_stk[w])) {
+            if (lane == 0) *overflow = 1;
+            continue;
+        }
+        // centroid and covariance of the K neighbours (lanes 0..K-1), FP64 warp sums
+        double p[3] = {0.0, 0.0, 0.0};
+        if (lane < K) {
+            const float4 q = __ldg(ix.pts + t.j);
+            p[0] = q.x;
+            p[1] = q.y;
+            p[2] = q.z;
+        }
+        double c[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v = p[a];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            c[a] = v / (double)K;
+        }
+        double e[6] = {0, 0, 0, 0, 0, 0};
+        if (lane < K) {
+            const double x = p[0] - c[0], y = p[1] - c[1], z = p[2] - c[2];
+            e[0] = x * x;
+            e[1] = x * y;
+            e[2] = x * z;
+            e[3] = y * y;
+            e[4] = y * z;
+            e[5] = z * z;
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e[a] += __shfl_xor_sync(0xffffffffu, e[a], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int a = 0; a < 6; ++a) cov[6 * (size_t)i + a] = e[a] / (double)K;
+        }
+    }
+}
+
+// Eigenvector of the smallest eigenvalue of each 3x3 covariance (cyclic Jacobi
+// in FP64), turned so that n . (viewpoint - q) >= 0, written at the point's
+// original index.
+__global__ void k_normal_from_cov(Index ix, const double *__restrict__ cov, double v0, double v1, double v2,
+                                  float *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ix.n) return;
+    double a[3][3], V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    const double *e = cov + 6 * (size_t)i;
+    a[0][0] = e[0];
+    a[0][1] = a[1][0] = e[1];
+    a[0][2] = a[2][0] = e[2];
+    a[1][1] = e[3];
+    a[1][2] = a[2][1] = e[4];
+    a[2][2] = e[5];
+    const int P[3] = {0, 0, 1}, Qi[3] = {1, 2, 2};
+    for (int sweep = 0; sweep < 32; ++sweep) {
+        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+        const double diag = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
+        if (!(off > 1e-18 * diag)) break;
+        for (int r = 0; r < 3; ++r) {
+            const int pp = P[r], qq = Qi[r];
+            if (a[pp][qq] == 0.0) continue;
+            const double th = (a[qq][qq] - a[pp][pp]) / (2.0 * a[pp][qq]);
+            const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            const double cs = 1.0 / sqrt(tt * tt + 1.0), sn = tt * cs;
+            for (int k = 0; k < 3; ++k) {   // a <- J^T a J
+                const double akp = a[k][pp], akq = a[k][qq];
+                a[k][pp] = cs * akp - sn * akq;
+                a[k][qq] = sn * akp + cs * akq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double apk = a[pp][k], aqk = a[qq][k];
+                a[pp][k] = cs * apk - sn * aqk;
+                a[qq][k] = sn * apk + cs * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {   // V <- V J
+                const double vkp = V[k][pp], vkq = V[k][qq];
+                V[k][pp] = cs * vkp - sn * vkq;
+                V[k][qq] = sn * vkp + cs * vkq;
+            }
+        }
+    }
+    int m = 0;
+    if (a[1][1] < a[m][m]) m = 1;
+    if (a[2][2] < a[m][m]) m = 2;
+    double n[3] = {V[0][m], V[1][m], V[2][m]};
+    const double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    const float4 q = __ldg(ix.pts + i);
+    const double side = n[0] * (v0 - (double)q.x) + n[1] * (v1 - (double)q.y) + n[2] * (v2 - (double)q.z);
+    const double sg = side < 0.0 ? -inv : inv;
+    const int o = __float_as_int(q.w);
+    out[3 * (size_t)o] = (float)(n[0] * sg);
+    out[3 * (size_t)o + 1] = (float)(n[1] * sg);
+    out[3 * (size_t)o + 2] = (float)(n[2] * sg);
+}
+
 __global__ void k_median(const double *v, int n, double *out) {
     double a, b;
     block_median_pair(v, n, &a, &b);
@@ -604,6 +870,37 @@ cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
     if (sh) cudaFreeAsync(sh, s);
     if (out) cudaFreeAsync(out, s);
     if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
+
+cudaError_t estimate_normals(const TargetDev *t, int k, const double viewpoint[3], float *out_dev, cudaStream_t s,
+                             int *overflow_out) {
+    const int K = (int)std::min<int64_t>(k, t->n);
+    double *cov = nullptr;
+    int *flag = nullptr;
+    cudaError_t e = cudaMallocAsync(&cov, sizeof(double) * 6 * (size_t)t->n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&flag, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        const Index ix = make_index(*t);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t blocks = std::min<int64_t>((t->n + kKnnBlock / 32 - 1) / (kKnnBlock / 32),
+                                                 (int64_t)(sms > 0 ? sms : 152) * 16);
+        k_knn_cov<<<(unsigned)blocks, kKnnBlock, 0, s>>>(ix, K, cov, flag);
+        k_normal_from_cov<<<(unsigned)((t->n + 255) / 256), 256, 0, s>>>(ix, cov, viewpoint[0], viewpoint[1],
+                                                                         viewpoint[2], out_dev);
+        counters().launches += 2;
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    counters().d2h += sizeof(int);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (cov) cudaFreeAsync(cov, s);
+    if (flag) cudaFreeAsync(flag, s);
+    *overflow_out = h;
     return e;
 }
 

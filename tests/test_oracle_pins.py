@@ -465,3 +465,12 @@ def test_normal_minimises_the_rayleigh_quotient():
         qn = N[i] @ C @ N[i]
         assert qn <= np.einsum("nd,de,ne->n", U, C, U).min() + 1e-12
         assert abs(np.linalg.norm(N[i]) - 1.0) < 1e-12
+
+
+def test_normals_at_sampled_rows_equal_the_full_estimate():
+    g = np.random.default_rng(35)
+    Q = g.random((1500, 3)) * [1.0, 1.0, 0.05]
+    rows = np.arange(0, 1500, 13)
+    full = oracle.estimate_normals(Q, 30)
+    part = oracle.estimate_normals(Q, 30, rows=rows)
+    assert np.abs(full[rows] - part).max() < 1e-12
