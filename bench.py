@@ -32,7 +32,13 @@ one-registration-at-a-time GPU path on the same inputs (rank 0 only):
   --workload precision  workload 3 (Welsch point-to-plane, ellipsoids N = 500k,
                       M = 200k) in the three precision modes side by side:
                       time, queries/s and each mode's difference from the FP64
-                      reference mode.
+                      reference mode;
+  --workload robustness  random initial alignments as one batched launch: the
+                      source rotated from its ground-truth position by
+                      beta in {5, 10, 20, 30, 50} degrees about 10 random axes,
+                      three solvers (150 registrations); mean RMSE (Eq. 13) per
+                      beta, alpha-recall, and fixed nu_max / fixed nu_min /
+                      decreasing nu for the Welsch point-to-point solver.
 """
 from __future__ import annotations
 
@@ -68,7 +74,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serve", "precision"])
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batched", "serve", "precision", "robustness"])
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate (serve)")
     return ap.parse_args()
 
@@ -614,6 +621,75 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+def rmse_of(P, R, t, R_gt, t_gt) -> float:
+    """Eq. (13): RMSE between the computed and the ground-truth motion of P."""
+    import numpy as np
+    P = P.astype(np.float64)
+    d = P @ (np.asarray(R_gt) - np.asarray(R)).T + (np.asarray(t_gt) - np.asarray(t))
+    return float(np.sqrt((d * d).sum(axis=1).mean()))
+
+
+def run_robustness(args):
+    import numpy as np
+    import torch
+
+    from paper_2007_07627_gb300 import synth
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2007_07627_gb300 as fr
+    # stand-in for the paper's failing scan pair with 50% added outliers
+    pair = synth.ellipsoid_pair(synth.CONFIG_SEEDS[3] + 100, M=40000, N=40000, overlap=1.0, noise=0.003,
+                                outliers=0.5, max_angle=0.0)
+    starts = synth.robustness_starts(pair)
+    variants = ("p2p", "p2p_welsch", "p2pl_welsch")
+    t = fr.target_create(pair.Q, pair.normals)
+    Pd = torch.from_numpy(pair.P).cuda()
+    cases = [(v, ang, T0) for v in variants for ang, T0 in starts]
+    prms = [fr.params_default(v) for v, _, _ in cases]
+    T0s = np.stack([T0 for _, _, T0 in cases])
+    fr.batch_register([t] * len(cases), [Pd] * len(cases), prms, T0=T0s)     # warm-up (and autotune)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = fr.batch_register([t] * len(cases), [Pd] * len(cases), prms, T0=T0s)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    alone = [fr.register(t, Pd, T0=T0, params=prm) for (_, _, T0), prm in zip(cases, prms)]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    err = [rmse_of(pair.P, r["R"], r["t"], pair.R_gt, pair.t_gt) / pair.diag for r in res]
+    per_angle = {v: {} for v in variants}
+    for (v, ang, _), e in zip(cases, err):
+        per_angle[v].setdefault(ang, []).append(e)
+    alphas = [10.0 ** x for x in np.arange(-5, -0.9, 0.5)]
+    recall = {v: [float(np.mean([e < a for (vv, _, _), e in zip(cases, err) if vv == v])) for a in alphas]
+              for v in variants}
+    # Fig. 4: fixed nu = nu_max, fixed nu = nu_min, decreasing nu (Welsch point-to-point, beta = 10 deg)
+    T10 = [T0 for ang, T0 in starts if ang == 10][0]
+    dyn = fr.register(t, Pd, T0=T10, params=fr.params_default("p2p_welsch"))
+    fixed = {}
+    for name, nu in (("nu_max", dyn["nu_max"]), ("nu_min", dyn["nu_min"])):
+        r = fr.register(t, Pd, T0=T10, params=fr.params_default("p2p_welsch", nu_max=nu, nu_min=nu))
+        fixed[name] = rmse_of(pair.P, r["R"], r["t"], pair.R_gt, pair.t_gt) / pair.diag
+    fixed["decreasing"] = rmse_of(pair.P, dyn["R"], dyn["t"], pair.R_gt, pair.t_gt) / pair.diag
+    t.destroy()
+    line = {"metric": "registrations/s of the batched sweep; mean RMSE/diag per initial angle",
+            "workload": "robustness", "value": len(cases) / t_batch, "unit": "regs/s", "higher_is_better": True,
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"pair": f"ellipsoids M={pair.M} N={pair.N}, full overlap, noise 0.003 diag, 50% outliers",
+                       "angles_deg": [5, 10, 20, 30, 50], "axes_per_angle": 10, "registrations": len(cases)},
+            "batched_s": t_batch, "plain_s": t_plain, "speedup_vs_plain": t_plain / t_batch,
+            "equal_results": sum(same_result(a, b) for a, b in zip(res, alone)), "of": len(cases),
+            "mean_rmse_over_diag": {v: {str(a): float(np.mean(e)) for a, e in d.items()} for v, d in per_angle.items()},
+            "alpha_recall": {"alpha": alphas, **recall},
+            "nu_schedule_rmse_over_diag": fixed}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -624,6 +700,8 @@ def main():
         run_serve(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "robustness":
+        run_robustness(args)
     else:
         run_ours(args)
 

@@ -22,7 +22,7 @@ from scipy.spatial.transform import Rotation
 __all__ = [
     "Pair", "rng", "random_rigid", "torus_pair", "height_field_pair",
     "ellipsoid_pair", "config_pair", "CONFIG_SEEDS", "BATCH_VARIANTS", "batch_specs", "make_pair",
-    "batch_pairs", "serve_specs", "serve_requests",
+    "batch_pairs", "serve_specs", "serve_requests", "rotation_about", "robustness_starts",
 ]
 
 # Seed of workload i (1-based) is 20070762 + i.
@@ -306,3 +306,34 @@ def serve_specs(seed: int = CONFIG_SEEDS[5], n: int = 64, lo: int = 1000, hi: in
 def serve_requests(seed: int = CONFIG_SEEDS[5], n: int = 64, lo: int = 1000, hi: int = 1_000_000) -> list:
     """serve_specs built into (variant, Pair) requests."""
     return [make_pair(s) for s in serve_specs(seed, n, lo, hi)]
+
+
+# ----------------------------------------------------------------------------
+# Random initial alignments (Sec. 6.4 limitations experiment)
+# ----------------------------------------------------------------------------
+
+def rotation_about(axis, angle_rad: float, centre) -> np.ndarray:
+    """4x4 rotation by `angle_rad` about the unit `axis` through `centre`."""
+    a = np.asarray(axis, dtype=np.float64)
+    R = Rotation.from_rotvec(a / np.linalg.norm(a) * angle_rad).as_matrix()
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = np.asarray(centre, np.float64) - R @ np.asarray(centre, np.float64)
+    return T
+
+
+def robustness_starts(pair: Pair, angles_deg=(5, 10, 20, 30, 50), per_angle: int = 10, seed: int = 20070770):
+    """Initial transforms that rotate the source from its ground-truth position
+    by a fixed angle about a random axis (uniform on the sphere) through the
+    aligned source's centroid, `per_angle` axes per angle. Returns a list of
+    (angle_deg, T0) with T0 = Rot o T_gt (x -> R_gt x + t_gt first)."""
+    g = rng(seed)
+    T_gt = np.eye(4)
+    T_gt[:3, :3] = pair.R_gt
+    T_gt[:3, 3] = pair.t_gt
+    centre = (pair.P.astype(np.float64) @ pair.R_gt.T + pair.t_gt).mean(axis=0)
+    out = []
+    for ang in angles_deg:
+        for _ in range(per_angle):
+            out.append((ang, rotation_about(_unit(g.standard_normal(3)), math.radians(ang), centre) @ T_gt))
+    return out

@@ -84,7 +84,7 @@ def _permuted(pair, seed):
     return pair.P[perm]
 
 
-def oracle_reference(pair, variant, over, perms=(1, 2), jitters=0, jitter=1e-13):
+def oracle_reference(pair, variant, over, perms=(1, 2), jitters=0, jitter=1e-13, T0=None):
     """Oracle run plus runs on permuted copies of the source (a permutation only
     changes the FP64 summation order) and `jitters` runs whose alignment solves
     carry a seeded rigid perturbation of size `jitter` (the rounding scale at
@@ -95,12 +95,12 @@ def oracle_reference(pair, variant, over, perms=(1, 2), jitters=0, jitter=1e-13)
     import dataclasses
     import oracle
     prm = oracle.Params(variant=variant, **over)
-    base = oracle.register(pair.P, pair.Q, prm, normals=pair.normals)
+    base = oracle.register(pair.P, pair.Q, prm, normals=pair.normals, T0=T0)
     stable, horizon, spread_ang, spread_t, energies = True, len(base["trace"]), 0.0, 0.0, [base["final_energy"]]
     runs = [(_permuted(pair, s), prm) for s in perms]
     runs += [(pair.P, dataclasses.replace(prm, solve_jitter=jitter, jitter_seed=s)) for s in range(1, jitters + 1)]
     for P, prm_k in runs:
-        r = oracle.register(P, pair.Q, prm_k, normals=pair.normals)
+        r = oracle.register(P, pair.Q, prm_k, normals=pair.normals, T0=T0)
         for key in ("iterations", "corr_passes", "reverts", "line_search_trials", "stages"):
             stable &= r[key] == base[key]
         n = min(len(r["trace"]), len(base["trace"]))
