@@ -367,7 +367,7 @@ def nu_min_point_to_plane(Qn: np.ndarray, Nq: np.ndarray) -> float:
 # Parameters and results
 # ---------------------------------------------------------------------------
 
-VARIANTS = ("p2p", "p2p_welsch", "p2pl_welsch")
+VARIANTS = ("p2p", "p2p_welsch", "p2pl_welsch", "p2pl")
 
 
 @dataclasses.dataclass
@@ -560,7 +560,12 @@ def se3_transform(xi) -> np.ndarray:
 
 
 def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
-    """Algorithm 2 (Welsch point-to-plane ICP with AA)."""
+    """Algorithm 2 (Welsch point-to-plane ICP with AA). params.variant 'p2pl'
+    runs the plain point-to-plane objective of Eq. (15) the same way. Reading:
+    psi(x) = x^2, so gamma_i = 1 and the energy is sum H_i^2, and a single stage
+    whose iteration cap is max_iters (the caps 6..10 of Sec. 5 belong to the nu
+    stages, which plain point-to-plane does not have)."""
+    robust = params.variant == "p2pl_welsch"
     P = np.asarray(P32, dtype=np.float64)
     Q = np.asarray(Q32, dtype=np.float64)
     Nr = np.asarray(N32, dtype=np.float64)       # normals used as given
@@ -577,7 +582,10 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
         idx, _, _ = closest(apply(T, Pn), Qn)
         n = Nr[idx]
         B = np.einsum("nd,nd->n", apply(T, Pn) - Qn[idx], n)
-        E = float(welsch(B, nu).sum()) if nu is not None else None
+        if robust:
+            E = float(welsch(B, nu).sum()) if nu is not None else None
+        else:
+            E = float((B * B).sum())
         return dict(xi=np.array(xi, dtype=np.float64), idx=idx, B=B, n=n, E=E)
 
     _, jit_xi = _jitter(params)
@@ -590,7 +598,7 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
         B_i - J_i^T xi_k maps a true fixed point away from itself.
         """
         xi = ev["xi"]
-        gamma = np.exp(-ev["B"] ** 2 / (2.0 * nu * nu))
+        gamma = np.exp(-ev["B"] ** 2 / (2.0 * nu * nu)) if robust else np.ones_like(ev["B"])
         J = plane_gradient(xi, Pn, ev["n"])
         A = (J * gamma[:, None]).T @ J
         b = (J * gamma[:, None]).T @ (J @ xi - ev["B"])
@@ -602,12 +610,16 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
 
     xi0 = np.zeros(6) if T0 is None else se3_vee(se3_log(nz.T_to_normalized(np.asarray(T0, np.float64))))
     ev_prev = evaluate(xi0, None)
-    nu_max = params.nu_max if params.nu_max > 0 else 3.0 * float(np.median(np.abs(ev_prev["B"])))
-    nu_min = params.nu_min if params.nu_min > 0 else nu_min_point_to_plane(Qn, Nr)
-    nu_min = max(nu_min, params.nu_min_floor)
-    nu_max = max(nu_max, nu_min)
+    if robust:
+        nu_max = params.nu_max if params.nu_max > 0 else 3.0 * float(np.median(np.abs(ev_prev["B"])))
+        nu_min = params.nu_min if params.nu_min > 0 else nu_min_point_to_plane(Qn, Nr)
+        nu_min = max(nu_min, params.nu_min_floor)
+        nu_max = max(nu_max, nu_min)
+        cap = params.p2pl_iters_first
+    else:                                             # one stage (nu unused)
+        nu_max = nu_min = 1.0
+        cap = params.max_iters
     nu = nu_max
-    cap = params.p2pl_iters_first
     x_prev = xi0
     xk = xi0
     E_prev = math.inf
@@ -677,7 +689,7 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
             if nu == nu_min:
                 break
             nu = max(nu / 2.0, nu_min)
-            cap = min(cap + 1, params.p2pl_iters_cap)
+            cap = min(cap + 1, params.p2pl_iters_cap)   # robust only: plain has one stage
             x_prev = xk
             ev_prev = ev_last
     except Degenerate:
@@ -688,7 +700,7 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
 def register(P32, Q32, params: Params, normals=None, T0=None) -> dict:
     if params.variant in ("p2p", "p2p_welsch"):
         return register_point_to_point(P32, Q32, params, T0)
-    if params.variant == "p2pl_welsch":
+    if params.variant in ("p2pl_welsch", "p2pl"):
         if normals is None:
             raise ValueError("point-to-plane needs target normals")
         return register_point_to_plane(P32, Q32, normals, params, T0)

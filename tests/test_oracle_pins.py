@@ -346,9 +346,19 @@ def test_plain_mm_energy_is_monotone(variant):
 
 
 def test_safeguard_keeps_accepted_energy_monotone():
-    P, Q, _, _, _ = _surface_pair(15, n=500, angle=0.3, noise=0.003)
+    P, Q, N, _, _ = _surface_pair(15, n=500, angle=0.3, noise=0.003)
     r = oracle.register(P, Q, oracle.Params(variant="p2p", max_iters=100))
     assert np.all(np.diff(r["trace"]) <= 0.0)
+    # plain point-to-plane: one stage, the line search keeps the accepted energy monotone too
+    r = oracle.register(P, Q, oracle.Params(variant="p2pl", max_iters=100), normals=N)
+    assert r["stages"] == 1 and np.all(np.diff(r["trace"]) <= 0.0)
+
+
+def test_plain_point_to_plane_has_one_stage_capped_by_max_iters():
+    P, Q, N, _, _ = _surface_pair(19, n=400, angle=0.2, noise=0.004)
+    r = oracle.register(P, Q, oracle.Params(variant="p2pl", max_iters=3), normals=N)
+    assert r["stages"] == 1 and r["iterations"] <= 3
+    assert r["nu_max"] == 1.0 and r["nu_min"] == 1.0
 
 
 def test_safeguard_reverts_bad_anderson_steps(monkeypatch):
@@ -365,7 +375,7 @@ def test_safeguard_reverts_bad_anderson_steps(monkeypatch):
     assert np.allclose(bad["trace"], plain["trace"], rtol=1e-10, atol=0)
 
 
-@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch", "p2pl_welsch"])
+@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch", "p2pl_welsch", "p2pl"])
 def test_exact_copy_is_recovered(variant):
     P, Q, N, R, t = _surface_pair(17, n=800, angle=0.15)
     r = oracle.register(P, Q, oracle.Params(variant=variant), normals=N)
@@ -373,7 +383,7 @@ def test_exact_copy_is_recovered(variant):
     # float32 inputs: the copy is exact only to float32 rounding
     assert np.abs(r["R"] - R).max() < 1e-5
     assert np.abs(r["t"] - t).max() < 1e-5
-    if variant == "p2p":
+    if variant in ("p2p", "p2pl"):
         assert r["final_energy"] < 1e-9
 
 
