@@ -602,11 +602,21 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
         J = plane_gradient(xi, Pn, ev["n"])
         A = (J * gamma[:, None]).T @ J
         b = (J * gamma[:, None]).T @ (J @ xi - ev["B"])
+        # Reading for points in a plane (Sec. 3: the problem is stated in R^d):
+        # embedded at z = 0 with in-plane normals, the directions that tilt the
+        # plane or move along z change no distance, so their rows, columns and
+        # right-hand sides are exactly zero; they keep a zero step and the rest
+        # is the 2-D system. 3-D data has no such direction.
+        act = ~((A == 0.0).all(axis=1) & (A == 0.0).all(axis=0) & (b == 0.0))
+        if not act.any():
+            raise Degenerate("singular point-to-plane system")
+        x = np.zeros(6)
         try:
-            cf = sla.cho_factor(A)
+            cf = sla.cho_factor(A[np.ix_(act, act)])
         except np.linalg.LinAlgError as e:
             raise Degenerate("singular point-to-plane system") from e
-        return jit_xi(sla.cho_solve(cf, b))
+        x[act] = sla.cho_solve(cf, b[act])
+        return jit_xi(x)
 
     xi0 = np.zeros(6) if T0 is None else se3_vee(se3_log(nz.T_to_normalized(np.asarray(T0, np.float64))))
     ev_prev = evaluate(xi0, None)

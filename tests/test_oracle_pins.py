@@ -484,3 +484,59 @@ def test_normals_at_sampled_rows_equal_the_full_estimate():
     full = oracle.estimate_normals(Q, 30)
     part = oracle.estimate_normals(Q, 30, rows=rows)
     assert np.abs(full[rows] - part).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Points in the plane (Sec. 3 states the problem in R^d)
+# --------------------------------------------------------------------------
+
+def test_planar_procrustes_is_the_2d_closed_form():
+    """On points with z = 0 the 3-D alignment step is the 2-D one: a rotation
+    about z by atan2(sum w (p x q)_z, sum w p . q) of the centred sets, and a
+    translation in the plane."""
+    g = np.random.default_rng(51)
+    P = np.column_stack([g.random((300, 2)), np.zeros(300)])
+    th = 0.7
+    R2 = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    Q = np.column_stack([P[:, :2] @ R2.T + [0.3, -0.2] + 0.01 * g.standard_normal((300, 2)), np.zeros(300)])
+    w = g.random(300)
+    T = oracle.weighted_procrustes(P, Q, w)
+    pb, qb = (w[:, None] * P).sum(0) / w.sum(), (w[:, None] * Q).sum(0) / w.sum()
+    pc, qc = P - pb, Q - qb
+    ang = np.arctan2((w * (pc[:, 0] * qc[:, 1] - pc[:, 1] * qc[:, 0])).sum(), (w * (pc * qc).sum(1)).sum())
+    R = np.eye(3)
+    R[:2, :2] = [[np.cos(ang), -np.sin(ang)], [np.sin(ang), np.cos(ang)]]
+    assert np.abs(T[:3, :3] - R).max() < 1e-12
+    assert np.abs(T[:3, 3] - (qb - R @ pb)).max() < 1e-12 and abs(T[2, 3]) < 1e-15
+
+
+def _flower(n, g, noise=0.0):
+    """Points on the planar curve r = 1 + 0.3 cos(5 th) (z = 0) and its in-plane unit normals."""
+    th = g.random(n) * 2 * np.pi
+    r = 1 + 0.3 * np.cos(5 * th)
+    dr = -1.5 * np.sin(5 * th)
+    P = np.column_stack([r * np.cos(th), r * np.sin(th), np.zeros(n)])
+    tan = np.column_stack([dr * np.cos(th) - r * np.sin(th), dr * np.sin(th) + r * np.cos(th), np.zeros(n)])
+    nrm = np.column_stack([tan[:, 1], -tan[:, 0], np.zeros(n)])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    if noise:
+        P[:, :2] += noise * g.standard_normal((n, 2))
+    return P, nrm
+
+
+@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch", "p2pl_welsch", "p2pl"])
+def test_planar_registration_stays_in_the_plane(variant):
+    """Points in the plane: every variant returns a rotation about z and a
+    translation in the plane, and recovers an exact planar copy."""
+    g = np.random.default_rng(52)
+    Q, N = _flower(1500, g)
+    th = 0.25
+    Rz = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    P = (Q[:1200] - [0.05, -0.02, 0.0]) @ Rz            # the copy, moved in the plane
+    r = oracle.register(P.astype(np.float32), Q.astype(np.float32), oracle.Params(variant=variant),
+                        normals=N.astype(np.float32))
+    assert r["status"] == "ok"
+    assert np.array_equal(r["R"][2], [0.0, 0.0, 1.0]) and np.array_equal(r["R"][:, 2], [0.0, 0.0, 1.0])
+    assert r["t"][2] == 0.0
+    # the copy to within the stopping rule (epsilon = 1e-5 on the change of the iterate)
+    assert np.abs(r["R"] - Rz).max() < 5e-5 and np.abs(P @ r["R"].T + r["t"] - Q[:1200]).max() < 5e-5
