@@ -11,7 +11,13 @@
  *                         (Sec. 4.2, "Fast ICP"): Algorithm 1 with psi(x) = x^2,
  *                         unit weights and a single stage;
  *   FRICP_P2P_WELSCH_AA   Welsch-robust point-to-point ICP (Sec. 4.3, Alg. 1);
- *   FRICP_P2PL_WELSCH_AA  Welsch-robust point-to-plane ICP (Sec. 5, Alg. 2).
+ *   FRICP_P2PL_WELSCH_AA  Welsch-robust point-to-plane ICP (Sec. 5, Alg. 2);
+ *   FRICP_P2PL_AA         plain point-to-plane ICP (Sec. 5, Eq. 15) with the
+ *                         Gauss-Newton / Anderson / line-search scheme of
+ *                         Alg. 2 and psi(x) = x^2.
+ * Points in the plane (the paper states the problem in R^d, Sec. 3) are
+ * registered as 3-D points with z = 0: the result is then a rotation about z
+ * and a translation in the plane (see the 2-D tests).
  *
  * Conventions for every call:
  *   - Point arrays are contiguous float32 [n][3] (x, y, z); normals likewise.
@@ -54,7 +60,9 @@ typedef enum {
 typedef enum {
     FRICP_P2P_AA = 0,
     FRICP_P2P_WELSCH_AA = 1,
-    FRICP_P2PL_WELSCH_AA = 2
+    FRICP_P2PL_WELSCH_AA = 2,
+    FRICP_P2PL_AA = 3        /* plain point-to-plane ICP (Eq. 15) solved like Alg. 2 with psi(x) = x^2:
+                                weights 1, energy sum H_i^2, one stage capped by max_iters */
 } fricp_variant;
 
 /* Arithmetic of the correspondence search and the per-point terms. The sums,
@@ -266,6 +274,7 @@ fricp_status fricp_closest_points(const fricp_target *target, const float *p_xyz
  *     alignment step (Eq. 4 / Eq. 12).
  *   variant P2PL_WELSCH_AA: out[0] = E~ (sum psi_nu(H_i), Eq. 15),
  *     out[1..6] = xi* = G_ppl(xi) (Eq. 19) for xi = log(T) = [delta; u].
+ *   variant P2PL_AA: as P2PL_WELSCH_AA with weights 1 and out[0] = sum H_i^2.
  *   out[16..43]: the reduced FP64 sums of the pass. Point-to-point (17 values):
  *     sum w, sum w p~ (3), sum w q~ (3), sum w p~ q~^T (9, row-major), E, with
  *     p~ = p - center, q~ = q - center in the caller's units. Point-to-plane

@@ -22,8 +22,8 @@ __all__ = [
     "closest_points", "eval_pass", "target_nu_min", "version", "counters",
 ]
 
-P2P_AA, P2P_WELSCH_AA, P2PL_WELSCH_AA = 0, 1, 2
-VARIANTS = {"p2p": P2P_AA, "p2p_welsch": P2P_WELSCH_AA, "p2pl_welsch": P2PL_WELSCH_AA}
+P2P_AA, P2P_WELSCH_AA, P2PL_WELSCH_AA, P2PL_AA = 0, 1, 2, 3
+VARIANTS = {"p2p": P2P_AA, "p2p_welsch": P2P_WELSCH_AA, "p2pl_welsch": P2PL_WELSCH_AA, "p2pl": P2PL_AA}
 PREC_FP64, PREC_FP32, PREC_FP16_STORAGE = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp16": PREC_FP16_STORAGE}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EDEGENERATE", 6: "EUNSUPPORTED",

@@ -139,7 +139,7 @@ const char *fricp_last_error(void) { return g_err.c_str(); }
 
 fricp_status fricp_params_default(int32_t variant, fricp_params *out) {
     if (out == nullptr) return fail(FRICP_EINVAL, "out is NULL");
-    if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_WELSCH_AA) return fail(FRICP_EINVAL, "unknown variant");
+    if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_AA) return fail(FRICP_EINVAL, "unknown variant");
     std::memset(out, 0, sizeof(*out));
     out->variant = variant;
     out->anderson_m = 5;
@@ -248,12 +248,12 @@ int32_t fricp_target_has_normals(const fricp_target *t) { return t ? t->d.has_no
 fricp_status fricp_target_nu_min(const fricp_target *t, int32_t variant, double scale, void *stream,
                                  double *nu_min_out) {
     if (!t || !nu_min_out) return fail(FRICP_EINVAL, "NULL argument");
-    if (variant == FRICP_P2PL_WELSCH_AA && !t->d.has_normals)
+    if (fricp::variant_p2pl(variant) && !t->d.has_normals)
         return fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");
     Ordered ord(stream);
     cudaError_t e = fricp::target_nu_stats(const_cast<TargetDev *>(&t->d), ord.work);
     if (e != cudaSuccess) return cuda_fail(e, "nu_min statistics");
-    *nu_min_out = variant == FRICP_P2PL_WELSCH_AA ? scale * t->d.H_Q / 6.0 : scale * t->d.E_Q / (3.0 * std::sqrt(3.0));
+    *nu_min_out = fricp::variant_p2pl(variant) ? scale * t->d.H_Q / 6.0 : scale * t->d.E_Q / (3.0 * std::sqrt(3.0));
     return FRICP_OK;
 }
 
@@ -283,7 +283,7 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     fricp_status st = check_params(params);
     if (st != FRICP_OK) return st;
     const fricp_params prm = *params;
-    if (prm.variant == FRICP_P2PL_WELSCH_AA && !t->d.has_normals)
+    if (fricp::variant_p2pl(prm.variant) && !t->d.has_normals)
         return fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");
     if (T0)
         for (int i = 0; i < 16; ++i)
@@ -296,7 +296,7 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     if (st != FRICP_OK) return st;
 
     const int ntiles = (int)((m + fricp::kBlock - 1) / fricp::kBlock);
-    const bool robust = prm.variant != FRICP_P2P_AA;
+    const bool robust = fricp::variant_robust(prm.variant);
     DevBuf<float4> src;
     DevBuf<PairState> st_dev;
     DevBuf<double> partial, resid, trace_dev;
@@ -363,11 +363,11 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
                              const double *center, void *stream, double *out) {
     if (!t || !p_xyz || !T_normalized || !out) return fail(FRICP_EINVAL, "NULL argument");
     if (m < 1 || m > (int64_t)1 << 30) return fail(FRICP_EINVAL, "m must be in 1..2^30");
-    if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_WELSCH_AA) return fail(FRICP_EINVAL, "unknown variant");
-    if (variant == FRICP_P2PL_WELSCH_AA && !t->d.has_normals)
+    if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_AA) return fail(FRICP_EINVAL, "unknown variant");
+    if (fricp::variant_p2pl(variant) && !t->d.has_normals)
         return fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");
     if (!(scale > 0.0)) return fail(FRICP_EINVAL, "scale must be > 0");
-    if (variant != FRICP_P2P_AA && !(nu > 0.0)) return fail(FRICP_EINVAL, "nu must be > 0");
+    if (fricp::variant_robust(variant) && !(nu > 0.0)) return fail(FRICP_EINVAL, "nu must be > 0");
     Ordered ord(stream);
     const cudaStream_t s = ord.work;
     DevInput p;
@@ -391,7 +391,7 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     fricp_params_default(variant, &prm);
     const double c[3] = {center ? center[0] : 0.0, center ? center[1] : 0.0, center ? center[2] : 0.0};
     PairState h = initial_state(prm, m, ntiles, scale, c, 1.0, 0);
-    h.nu = variant == FRICP_P2P_AA ? 1.0 : nu;
+    h.nu = fricp::variant_robust(variant) ? nu : 1.0;
     double T12[12];
     for (int r = 0; r < 3; ++r) {
         for (int k = 0; k < 3; ++k) T12[3 * r + k] = T_normalized[4 * r + k];

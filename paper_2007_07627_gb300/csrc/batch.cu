@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ sl
         const Slot sl = slots[p];
         const int i0 = lt * kBlock + sub * chunk;
         const int i1 = min(i0 + chunk, h.M);
-        const bool p2p = h.variant != FRICP_P2PL_WELSCH_AA;
+        const bool p2p = !fricp::variant_p2pl(h.variant);
         for (int i = i0; i < i1; ++i) {
             bool ok;
             if (h.prec == PREC_FP32)
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_accum_batch(const Slot *__restric
         copy_head(heads + p, &h, threadIdx.x, kBlock);
         const Slot sl = slots[p];
         __syncthreads();
-        if (h.variant == FRICP_P2PL_WELSCH_AA) {
+        if (fricp::variant_p2pl(h.variant)) {
             bool last;
             if (h.prec == PREC_FP32)
                 last = accum_tile<1, PREC_FP32>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
@@ -536,7 +536,7 @@ fricp_status check_pair(const fricp_target *t, const float *p, int64_t m, const 
     if (m < 1 || m > (int64_t)1 << 30) return fail(FRICP_EINVAL, "m must be in 1..2^30");
     fricp_status st = check_params(prm);
     if (st != FRICP_OK) return st;
-    if (prm->variant == FRICP_P2PL_WELSCH_AA && !fricp::target_dev(t)->has_normals)
+    if (fricp::variant_p2pl(prm->variant) && !fricp::target_dev(t)->has_normals)
         return fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");
     if (T0)
         for (int i = 0; i < 16; ++i)

@@ -48,6 +48,11 @@ constexpr double kWelschCut = 750.0;
 //              bucket's box (8 B per point); ties to the lowest bucket-order position.
 enum Prec : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_FP16 = 2 };
 
+// Variant families: point-to-plane (the Alg. 2 scheme, 28 sums) and robust
+// (Welsch weights and nu stages).
+__host__ __device__ inline bool variant_p2pl(int v) { return v == FRICP_P2PL_WELSCH_AA || v == FRICP_P2PL_AA; }
+__host__ __device__ inline bool variant_robust(int v) { return v == FRICP_P2P_WELSCH_AA || v == FRICP_P2PL_WELSCH_AA; }
+
 struct Index {
     const float4 *pts;
     const float4 *nrm;

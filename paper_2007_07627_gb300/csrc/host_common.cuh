@@ -64,7 +64,7 @@ inline bool host_finite(const float *x, int64_t n3) {
 }
 
 inline fricp_status check_params(const fricp_params *p) {
-    if (p->variant < FRICP_P2P_AA || p->variant > FRICP_P2PL_WELSCH_AA) return fail(FRICP_EINVAL, "unknown variant");
+    if (p->variant < FRICP_P2P_AA || p->variant > FRICP_P2PL_AA) return fail(FRICP_EINVAL, "unknown variant");
     if (p->anderson_m < 0 || p->anderson_m > fricp::kMaxM) return fail(FRICP_EINVAL, "anderson_m must be in 0..5");
     if (p->max_iters < 1 || p->p2pl_iters_first < 1 || p->p2pl_iters_cap < p->p2pl_iters_first)
         return fail(FRICP_EINVAL, "iteration caps must be >= 1 and cap >= first");
@@ -213,6 +213,9 @@ inline PairState initial_state(const fricp_params &prm, int64_t m, int ntiles, d
     h.nu_min = nu_min;
     h.E_prev = INFINITY;
     h.cap = prm.p2pl_iters_first;
+    if (prm.variant == FRICP_P2PL_AA) {   // one stage: its cap is max_iters (the 6..10 caps belong to nu stages)
+        h.cap_first = h.cap_max = h.cap = prm.max_iters;
+    }
     return h;
 }
 
@@ -230,7 +233,7 @@ inline fricp_status setup_pair(const TargetDev &t, const fricp_params &prm, int6
         const cudaError_t e = build_fp16_storage(const_cast<TargetDev *>(&t), s);
         if (e != cudaSuccess) return cuda_fail(e, "FP16 target storage");
     }
-    const bool robust = prm.variant != FRICP_P2P_AA;
+    const bool robust = fricp::variant_robust(prm.variant);
     double nu_min = 1.0;
     if (robust) {
         if (prm.nu_min > 0.0) {
@@ -238,7 +241,7 @@ inline fricp_status setup_pair(const TargetDev &t, const fricp_params &prm, int6
         } else {
             const cudaError_t e = target_nu_stats(const_cast<TargetDev *>(&t), s);
             if (e != cudaSuccess) return cuda_fail(e, "nu_min statistics");
-            nu_min = prm.variant == FRICP_P2PL_WELSCH_AA ? *scale * t.H_Q / 6.0 : *scale * t.E_Q / (3.0 * std::sqrt(3.0));
+            nu_min = fricp::variant_p2pl(prm.variant) ? *scale * t.H_Q / 6.0 : *scale * t.E_Q / (3.0 * std::sqrt(3.0));
         }
         nu_min = std::fmax(nu_min, prm.nu_min_floor);
     }
@@ -246,7 +249,7 @@ inline fricp_status setup_pair(const TargetDev &t, const fricp_params &prm, int6
     *h = initial_state(prm, m, ntiles, *scale, c, nu_min, trace_cap);
     double T0n[12];
     to_normalised(T0, *scale, c, T0n);
-    if (prm.variant == FRICP_P2PL_WELSCH_AA) {
+    if (fricp::variant_p2pl(prm.variant)) {
         se3_log(T0n, h->xk);
         request_eval_xi(h, h->xk, 1);
     } else {
@@ -267,7 +270,7 @@ inline fricp_status setup_pair(const TargetDev &t, const fricp_params &prm, int6
 inline void fill_result(const PairState &r, int variant, double scale, const double c[3], int trace_cap,
                         fricp_result *out) {
     double Tn[12];
-    if (variant == FRICP_P2PL_WELSCH_AA)
+    if (fricp::variant_p2pl(variant))
         se3_exp(r.xk, Tn);
     else
         copy_n(Tn, r.Tk, 12);

@@ -333,33 +333,46 @@ FRICP_HD inline bool anderson_lstsq(double D[6][kMaxM], double f[6], int mk, dou
 }
 
 // Cholesky solve of a 6x6 symmetric positive-definite system; false if a pivot
-// is not positive and finite.
+// is not positive and finite. A direction whose row, column and right-hand
+// side are all exactly zero is left out and gets x_j = 0: the system of points
+// in a plane (z = 0, in-plane normals), where tilting the plane and moving along
+// z change no distance, is the 2-D system (Sec. 3 states the problem in R^d).
+// 3-D data never has such a direction, and then nothing changes.
 FRICP_HD inline bool chol6_solve(const double A_[36], const double b[6], double x[6]) {
+    int act[6], na = 0;
+    for (int j = 0; j < 6; ++j) {
+        bool zero = b[j] == 0.0;
+        for (int k = 0; k < 6 && zero; ++k) zero = A_[6 * j + k] == 0.0 && A_[6 * k + j] == 0.0;
+        x[j] = 0.0;
+        if (!zero) act[na++] = j;
+    }
+    if (na == 0) return false;
     double L[36];
     for (int i = 0; i < 36; ++i) L[i] = 0.0;
-    for (int j = 0; j < 6; ++j) {
-        double d = A_[6 * j + j];
+    for (int j = 0; j < na; ++j) {
+        double d = A_[7 * act[j]];
         for (int k = 0; k < j; ++k) d -= L[6 * j + k] * L[6 * j + k];
         if (!(d > 0.0) || !isfinite(d)) return false;
         const double il = rsqrt64(d);   // 1 / L_jj
         L[6 * j + j] = il;              // the diagonal holds the reciprocals
-        for (int i = j + 1; i < 6; ++i) {
-            double s = A_[6 * i + j];
+        for (int i = j + 1; i < na; ++i) {
+            double s = A_[6 * act[i] + act[j]];
             for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
             L[6 * i + j] = s * il;
         }
     }
-    double y[6];
-    for (int i = 0; i < 6; ++i) {
-        double s = b[i];
+    double y[6], z[6];
+    for (int i = 0; i < na; ++i) {
+        double s = b[act[i]];
         for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
         y[i] = s * L[6 * i + i];
     }
-    for (int i = 5; i >= 0; --i) {
+    for (int i = na - 1; i >= 0; --i) {
         double s = y[i];
-        for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
-        x[i] = s * L[6 * i + i];
+        for (int k = i + 1; k < na; ++k) s -= L[6 * k + i] * z[k];
+        z[i] = s * L[6 * i + i];
     }
+    for (int i = 0; i < na; ++i) x[act[i]] = z[i];
     return true;
 }
 

@@ -400,9 +400,9 @@ static __device__ __noinline__ void solver_step(PairState *st, const double *S, 
     st->device_steps++;
     if (st->eval_counts) st->corr_passes++;
     if (st->phase == PH_EVAL) {
-        st->eval_out[0] = S[st->variant == FRICP_P2PL_WELSCH_AA ? kSumsP2PL - 1 : kSumsP2P - 1];
+        st->eval_out[0] = S[fricp::variant_p2pl(st->variant) ? kSumsP2PL - 1 : kSumsP2P - 1];
         int ok;
-        if (st->variant == FRICP_P2PL_WELSCH_AA) {
+        if (fricp::variant_p2pl(st->variant)) {
             double d[6];
             ok = gn_delta(st->xeval, S, d);
             for (int i = 0; i < 6; ++i) st->eval_out[1 + i] = st->xeval[i] + d[i];
@@ -411,14 +411,14 @@ static __device__ __noinline__ void solver_step(PairState *st, const double *S, 
             ok = align_from_sums(st, S, T);
             for (int i = 0; i < 12; ++i) st->eval_out[1 + i] = T[i];
         }
-        const int K = st->variant == FRICP_P2PL_WELSCH_AA ? kSumsP2PL : kSumsP2P;
+        const int K = fricp::variant_p2pl(st->variant) ? kSumsP2PL : kSumsP2P;
         for (int k = 0; k < K; ++k) st->eval_out[16 + k] = S[k];
         st->status = ok ? FRICP_OK : FRICP_EDEGENERATE;
         st->phase = PH_DONE;
         st->done = 1;
         return;
     }
-    if (st->variant == FRICP_P2PL_WELSCH_AA)
+    if (fricp::variant_p2pl(st->variant))
         p2pl_step(st, S, trace);
     else
         p2p_step(st, S, trace);

@@ -79,12 +79,12 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
     if (!target || !p_xyz_dev || !T_normalized || !out) return static_fail(FRICP_EINVAL, "NULL argument");
     if (m < 1 || m > kStaticMaxPoints)
         return static_fail(FRICP_EINVAL, "m must be in 1..32768 for fricp_eval_pass_static");
-    if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_WELSCH_AA) return static_fail(FRICP_EINVAL, "unknown variant");
+    if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_AA) return static_fail(FRICP_EINVAL, "unknown variant");
     const fricp::TargetDev &td = *fricp::target_dev(target);
-    if (variant == FRICP_P2PL_WELSCH_AA && !td.has_normals)
+    if (fricp::variant_p2pl(variant) && !td.has_normals)
         return static_fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");
     if (!(scale > 0.0)) return static_fail(FRICP_EINVAL, "scale must be > 0");
-    if (variant != FRICP_P2P_AA && !(nu > 0.0)) return static_fail(FRICP_EINVAL, "nu must be > 0");
+    if (fricp::variant_robust(variant) && !(nu > 0.0)) return static_fail(FRICP_EINVAL, "nu must be > 0");
     char *base = nullptr;
     fricp_status st = scratch_address(&base);
     if (st != FRICP_OK) return st;
@@ -113,7 +113,7 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
     h.nu_min = 1.0;
     h.E_prev = INFINITY;
     h.cap = 6;
-    h.nu = variant == FRICP_P2P_AA ? 1.0 : nu;
+    h.nu = fricp::variant_robust(variant) ? nu : 1.0;
     double T12[12];
     for (int r = 0; r < 3; ++r) {
         for (int k = 0; k < 3; ++k) T12[3 * r + k] = T_normalized[4 * r + k];

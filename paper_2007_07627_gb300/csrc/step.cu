@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
     const int wpb = kBlock / 32;
     int *stk = s_stk[threadIdx.x >> 5];
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < h.M; i += gridDim.x * wpb) {
-        if (!search_query<PREC>(a.ix, a.src, a.prev, h, i, h.variant != FRICP_P2PL_WELSCH_AA, stk) &&
+        if (!search_query<PREC>(a.ix, a.src, a.prev, h, i, !fricp::variant_p2pl(h.variant), stk) &&
             (threadIdx.x & 31) == 0)
             a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
     }
@@ -80,7 +80,7 @@ __global__ void k_setup_eval(PairState *st, const double *T) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double Tn[12];
     for (int i = 0; i < 12; ++i) Tn[i] = T[i];
-    if (st->variant == FRICP_P2PL_WELSCH_AA) {
+    if (fricp::variant_p2pl(st->variant)) {
         double xi[6];
         se3_log(Tn, xi);
         request_eval_xi(st, xi, 1);
@@ -112,7 +112,7 @@ template <int PREC>
 void launch_step_prec(const StepArgs &a, int variant, int ntiles, cudaStream_t s, cudaEvent_t mid) {
     k_nn<PREC><<<nn_blocks<PREC>(ntiles * kBlock), kBlock, 0, s>>>(a);
     if (mid) cudaEventRecord(mid, s);
-    if (variant == FRICP_P2PL_WELSCH_AA)
+    if (fricp::variant_p2pl(variant))
         k_accum<1, PREC><<<ntiles, kBlock, 0, s>>>(a);
     else
         k_accum<0, PREC><<<ntiles, kBlock, 0, s>>>(a);

@@ -74,7 +74,7 @@ __device__ __forceinline__ void load_head(const PairState *st, StepHead &h) {
     h.phase = st->phase;
     h.variant = st->variant;
     h.prec = st->prec;
-    h.welsch = st->variant != FRICP_P2P_AA;
+    h.welsch = fricp::variant_robust(st->variant);
     h.M = st->M;
     for (int i = 0; i < 9; ++i) h.R[i] = st->Re[i];
     for (int r = 0; r < 3; ++r) {
@@ -184,7 +184,7 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
             const float4 nv = __ldg(ix.nrm + j);
             const float hh = s * fmaf(dz, nv.z, fmaf(dy, nv.y, dx * nv.x));
             if (h.phase == PH_INIT) resid[i] = (double)fabsf(hh);
-            const float g = expf(-hh * hh * i2);
+            const float g = h.welsch ? expf(-hh * hh * i2) : 1.0f;   // plain point-to-plane: weights 1
             float y[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
@@ -199,7 +199,7 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
                 for (int c = r; c < 6; ++c) acc[t++] = (double)(gz * z[c]);
                 acc[21 + r] = (double)(gz * hh);
             }
-            acc[27] = (double)(1.0f - g);
+            acc[27] = h.welsch ? (double)(1.0f - g) : (double)(hh * hh);
         }
         return;
     }
@@ -236,7 +236,7 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
         const double n0 = nv.x, n1 = nv.y, n2 = nv.z;
         const double hh = s * (dx * n0 + dy * n1 + dz * n2);
         if (h.phase == PH_INIT) resid[i] = fabs(hh);
-        const double g = exp(-hh * hh * h.inv2nu2);
+        const double g = h.welsch ? exp(-hh * hh * h.inv2nu2) : 1.0;   // plain point-to-plane: weights 1
         // y = R p~ in normalised units; z = [y x n; n]
         double y[3];
 #pragma unroll
@@ -250,7 +250,7 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
             for (int c = r; c < 6; ++c) acc[t++] = gz * z[c];
             acc[21 + r] = gz * hh;
         }
-        acc[27] = 1.0 - g;
+        acc[27] = h.welsch ? 1.0 - g : hh * hh;
     }
 }
 

@@ -60,8 +60,9 @@ def oracle_pass_p2p(P32, Q32, Tn, nu, scale, center, robust):
     return E, oracle.weighted_procrustes(Pn, Qn[idx], w)
 
 
-def oracle_pass_p2pl(P32, Q32, N32, Tn, nu, scale, center):
-    """Energy and xi* = G_ppl(xi) of one Alg. 2 pass at xi = log(Tn)."""
+def oracle_pass_p2pl(P32, Q32, N32, Tn, nu, scale, center, robust=True):
+    """Energy and xi* = G_ppl(xi) of one Alg. 2 pass at xi = log(Tn) (robust:
+    Welsch weights and energy; else weights 1 and energy sum B^2)."""
     nz = oracle.Normalization(c=np.asarray(center, float), s=scale)
     Pn, Qn = nz.fwd(np.asarray(P32, float)), nz.fwd(np.asarray(Q32, float))
     Nr = np.asarray(N32, float)
@@ -71,8 +72,8 @@ def oracle_pass_p2pl(P32, Q32, N32, Tn, nu, scale, center):
     idx, _, _ = oracle.closest(X, Qn)
     n = Nr[idx]
     B = np.einsum("nd,nd->n", X - Qn[idx], n)
-    E = float(oracle.welsch(B, nu).sum())
-    gamma = np.exp(-B ** 2 / (2 * nu * nu))
+    E = float(oracle.welsch(B, nu).sum()) if robust else float((B * B).sum())
+    gamma = np.exp(-B ** 2 / (2 * nu * nu)) if robust else np.ones_like(B)
     J = oracle.plane_gradient(xi, Pn, n)
     A = (J * gamma[:, None]).T @ J
     b = (J * gamma[:, None]).T @ (J @ xi - B)

@@ -95,7 +95,7 @@ def test_closest_points_workload_sampled(fr, cfg):
 # One fused pass
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch", "p2pl_welsch"])
+@pytest.mark.parametrize("variant", ["p2p", "p2p_welsch", "p2pl_welsch", "p2pl"])
 def test_single_pass_matches_oracle(fr, variant):
     pair = synth.config_pair(2, 0.05)
     P, Q = pair.P, pair.Q
@@ -106,8 +106,8 @@ def test_single_pass_matches_oracle(fr, variant):
         Tn = random_T(g, 0.3, 0.05) if trial else np.eye(4)
         nu = 0.02 + 0.1 * g.random()
         out = fr.eval_pass(t, P, variant, Tn, nu=nu, scale=nz.s, center=nz.c)
-        if variant == "p2pl_welsch":
-            E, xs, _ = oracle_pass_p2pl(P, Q, pair.normals, Tn, nu, nz.s, nz.c)
+        if variant in ("p2pl_welsch", "p2pl"):
+            E, xs, _ = oracle_pass_p2pl(P, Q, pair.normals, Tn, nu, nz.s, nz.c, robust=variant == "p2pl_welsch")
             assert abs(out[0] - E) <= 1e-10 * max(1.0, abs(E))
             assert np.abs(out[1:7] - xs).max() <= 1e-9
         else:
@@ -198,6 +198,9 @@ CASES = [
     ("ell50_out5", lambda: synth.config_pair(3, 0.01), "p2p", dict(max_iters=100)),
     ("ell50_out5", lambda: synth.config_pair(3, 0.01), "p2p_welsch", {}),
     ("ell50_out5", lambda: synth.config_pair(3, 0.01), "p2pl_welsch", {}),
+    ("torus", lambda: synth.config_pair(1), "p2pl", {}),
+    ("hf_full", lambda: _hf(3000, 4000, overlap=1.0, outliers=0.0, noise=0.001), "p2pl", {}),
+    ("ell_full", lambda: _ell(3000, 6000, overlap=1.0, outliers=0.0, noise=0.001), "p2pl", {}),
 ]
 
 
@@ -205,7 +208,7 @@ CASES = [
 def test_registration_matches_oracle(fr, name, make, variant, over):
     pair = make()
     ref = oracle_reference(pair, variant, over)
-    t = fr.target_create(pair.Q, pair.normals if variant == "p2pl_welsch" else None)
+    t = fr.target_create(pair.Q, pair.normals if variant.startswith("p2pl") else None)
     r_g = fr.register(t, pair.P, params=fr.params_default(variant, **over), trace_capacity=20000)
     assert_registration_parity(r_g, ref, pair.diag)
 
