@@ -341,7 +341,7 @@ FRICP_HD inline bool anderson_lstsq(double D[6][kMaxM], double f[6], int mk, dou
 FRICP_HD inline bool chol6_solve(const double A_[36], const double b[6], double x[6]) {
     int act[6], na = 0;
     for (int j = 0; j < 6; ++j) {
-        bool zero = b[j] == 0.0;
+        bool zero = b[j] == 0.0 && A_[7 * j] == 0.0;   // a zero row has a zero diagonal: test that first
         for (int k = 0; k < 6 && zero; ++k) zero = A_[6 * j + k] == 0.0 && A_[6 * k + j] == 0.0;
         x[j] = 0.0;
         if (!zero) act[na++] = j;

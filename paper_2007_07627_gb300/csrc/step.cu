@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
 // Accumulate kernel: one tile of points per block; the block that completes
 // the pass reduces the records and runs the solver step.
 template <int VAR, int PREC>
-__global__ void __launch_bounds__(kBlock) k_accum(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, 3) k_accum(StepArgs a) {
     constexpr int K = VAR ? kSumsP2PL : kSumsP2P;
     __shared__ StepHead h;
     __shared__ double red[K * kRedHalf];
