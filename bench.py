@@ -61,8 +61,8 @@ UNIT = "queries/s"
 VARIANT = "p2p_welsch"
 WORKLOAD = "welsch_p2p_aa_height_field_N100000_M80000"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
-CPU_SAMPLE_M = 40000                # cpu_baseline sample: half the source points, full target
-CPU_SAMPLE_ITERS = 5
+CPU_SAMPLE_M = 80000                # cpu_baseline sample: every source point, full target
+CPU_SAMPLE_ITERS = 10
 REF_SAMPLE_M = 16000                # --impl reference: 20% of the source points per step
 STEP_SOURCES = ["step.cu", "step_common.cuh", "fricp_internal.cuh", "solver.cuh", "linalg.cuh", "select.cuh"]
 

@@ -166,15 +166,31 @@ __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ sl
         const int i0 = lt * kBlock + sub * chunk;
         const int i1 = min(i0 + chunk, h.M);
         const bool p2p = !fricp::variant_p2pl(h.variant);
-        for (int i = i0; i < i1; ++i) {
-            bool ok;
-            if (h.prec == PREC_FP32)
-                ok = search_query<PREC_FP32>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
-            else if (h.prec == PREC_FP16)
-                ok = search_query<PREC_FP16>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
-            else
-                ok = search_query<PREC_FP64>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
-            if (!ok && lane == 0) sl.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+        if (p2p && h.welsch && h.phase != PH_INIT) {   // Welsch cap active: one query per warp (as k_nn)
+            for (int i = i0; i < i1; ++i) {
+                bool ok;
+                if (h.prec == PREC_FP32)
+                    ok = search_query<PREC_FP32>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
+                else if (h.prec == PREC_FP16)
+                    ok = search_query<PREC_FP16>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
+                else
+                    ok = search_query<PREC_FP64>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
+                if (!ok && lane == 0) sl.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+            }
+        } else {   // two queries per warp, one per half
+            int *hstk = stk + ((lane & 16) ? kHalfStack : 0);
+            for (int i2 = i0; i2 < i1; i2 += 2) {
+                const int i = i2 + ((lane & 16) ? 1 : 0);
+                const bool live = i < i1;
+                bool ok;
+                if (h.prec == PREC_FP32)
+                    ok = search_pair<PREC_FP32>(sl.ix, sl.src, sl.prev, h, i, live, p2p, hstk);
+                else if (h.prec == PREC_FP16)
+                    ok = search_pair<PREC_FP16>(sl.ix, sl.src, sl.prev, h, i, live, p2p, hstk);
+                else
+                    ok = search_pair<PREC_FP64>(sl.ix, sl.src, sl.prev, h, i, live, p2p, hstk);
+                if (!ok && lane == 0) sl.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+            }
         }
     }
 }

@@ -520,6 +520,138 @@ __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, in
 }
 
 // ---------------------------------------------------------------------------
+// Half-warp form of warp_nn: lanes 0-15 search one query and lanes 16-31
+// another, each half with its own lane state, its own stack (kHalfStack
+// entries) and its own rounds. A warm-started query pops about nine nodes per
+// round, so one query per warp leaves most lanes idle in the box tests; two
+// queries share the instruction stream instead. Every warp-wide primitive is
+// run by all 32 lanes and each half reads its own 16 bits; a half without a
+// query (`live` false) only takes part in them. Returns false (for both
+// halves) if either stack would overflow.
+// ---------------------------------------------------------------------------
+constexpr int kHalfStack = kWarpStack / 2;
+
+__device__ __forceinline__ void half_best(NNLane &q) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {   // xor below 16 stays inside the half
+        const float oh = __shfl_xor_sync(0xffffffffu, q.best_hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, q.best_lo, o);
+        const int oo = __shfl_xor_sync(0xffffffffu, q.best_orig, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, q.best_j, o);
+        const float of = __shfl_xor_sync(0xffffffffu, q.bestf, o);
+        if (lex_less(oh, ol, oo, q.best_hi, q.best_lo, q.best_orig)) {
+            q.best_hi = oh;
+            q.best_lo = ol;
+            q.best_orig = oo;
+            q.best_j = oj;
+        }
+        q.bestf = fminf(q.bestf, of);
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk, int start_leaf, bool live) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int hl = lane & 15;
+    const int hs = lane & 16;
+    const unsigned hmask = 0xffffu << hs;
+    const unsigned below = ((1u << hl) - 1u) << hs;
+    int depth = 0;
+    while ((1 << depth) < ix.L) ++depth;
+    if (live && start_leaf < 0) {   // cold: greedy descent (uniform within the half)
+        int node = 1;
+        while (node < ix.L) {
+            const float4 *b = ix.nodes + 4 * node;
+            const float d0 = box_d2(__ldg(b), __ldg(b + 1), q.xh, q.xl);
+            const float d1 = box_d2(__ldg(b + 2), __ldg(b + 3), q.xh, q.xl);
+            node = 2 * node + (d1 < d0 ? 1 : 0);
+        }
+        start_leaf = node - ix.L;
+    }
+    int sp = 0;
+    for (int lv0 = 0; lv0 < depth; lv0 += 16) {   // siblings of the path, root side first
+        const int lv = lv0 + hl;
+        int c = 0;
+        bool pass = false;
+        if (live && lv < depth) {
+            c = ((ix.L + start_leaf) >> (depth - 1 - lv)) ^ 1;
+            pass = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q.xh, q.xl) * kShrink <= q.bestf;
+        }
+        const unsigned m = __ballot_sync(FULL, pass) & hmask;
+        if (pass) stk[sp + __popc(m & below)] = c;
+        sp += __popc(m);
+    }
+    if (live) {
+        if (hl == 0) stk[sp] = ix.L + start_leaf;
+        ++sp;
+    }
+    __syncwarp();
+    const int leaf_parent_level = depth - 1;
+    bool ovf = false;
+    while (__any_sync(FULL, sp > 0)) {
+        const int k = min(16, sp);
+        const int node = (hl < k) ? stk[sp - 1 - hl] : 0;
+        sp -= k;
+        __syncwarp();
+        int c[4] = {0, 0, 0, 0};
+        bool ok[4] = {false, false, false, false};
+        bool leaf_ok = false;
+        if (node != 0) {
+            if (node < ix.L) {
+                const int level = 31 - __clz(node);
+                if (level < leaf_parent_level) {
+                    const float4 *b = ix.nodes + 8 * node;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        c[g] = 4 * node + g;
+                        ok[g] = box_d2(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q.xh, q.xl) * kShrink <= q.bestf;
+                    }
+                } else {
+                    const float4 *b = ix.nodes + 4 * node;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        c[g] = 2 * node + g;
+                        ok[g] = box_d2(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q.xh, q.xl) * kShrink <= q.bestf;
+                    }
+                }
+            } else {
+                leaf_ok = box_d2(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), q.xh, q.xl) * kShrink
+                          <= q.bestf;
+            }
+        }
+        int base = sp;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const unsigned mg = __ballot_sync(FULL, ok[g]) & hmask;
+            if (base + __popc(mg) > kHalfStack) ovf = true;
+            else if (ok[g]) stk[base + __popc(mg & below)] = c[g];
+            if (!ovf) base += __popc(mg);
+        }
+        sp = base;
+        if (__any_sync(FULL, ovf)) return false;
+        unsigned lm = __ballot_sync(FULL, leaf_ok) & hmask;
+        bool changed = false;
+        while (__any_sync(FULL, lm != 0u)) {   // one bucket per half per pass
+            const bool have = lm != 0u;
+            int src = lane;
+            if (have) {
+                src = __ffs(lm) - 1;
+                lm &= lm - 1u;
+            }
+            const int na = __shfl_sync(FULL, node, src);
+            if (have) {
+                const int j = (na - ix.L) * kLeaf + hl;
+                if (j < ix.n) changed |= nn_offer<PREC>(q, target_point<PREC>(ix, j), j);
+            }
+        }
+        if (__any_sync(FULL, changed)) half_best(q);
+        __syncwarp();
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (index.cu, step.cu). All return cudaError_t.
 // ---------------------------------------------------------------------------
 struct TargetDev {

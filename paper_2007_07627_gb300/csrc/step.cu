@@ -26,11 +26,24 @@ __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
     __syncthreads();
     if (h.done) return;
     const int wpb = kBlock / 32;
-    int *stk = s_stk[threadIdx.x >> 5];
-    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < h.M; i += gridDim.x * wpb) {
-        if (!search_query<PREC>(a.ix, a.src, a.prev, h, i, !fricp::variant_p2pl(h.variant), stk) &&
-            (threadIdx.x & 31) == 0)
-            a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+    const bool p2p = !fricp::variant_p2pl(h.variant);
+    if (p2p && h.welsch && h.phase != PH_INIT) {
+        // Welsch cap active: queries beyond it end after a round or two while the
+        // others search their neighbourhood, so a pair of queries would wait for
+        // the harder one: one query per warp
+        int *stk = s_stk[threadIdx.x >> 5];
+        for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < h.M; i += gridDim.x * wpb) {
+            if (!search_query<PREC>(a.ix, a.src, a.prev, h, i, p2p, stk) && (threadIdx.x & 31) == 0)
+                a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+        }
+    } else {
+        // similar work per query: two Morton-adjacent queries per warp, one per half
+        int *stk = s_stk[threadIdx.x >> 5] + (threadIdx.x & 16 ? kHalfStack : 0);
+        for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); 2 * e < h.M; e += gridDim.x * wpb) {
+            const int i = 2 * e + ((threadIdx.x & 16) ? 1 : 0);
+            if (!search_pair<PREC>(a.ix, a.src, a.prev, h, i, i < h.M, p2p, stk) && (threadIdx.x & 31) == 0)
+                a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+        }
     }
 }
 
@@ -104,7 +117,7 @@ int nn_blocks(int M) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nn<PREC>, kBlock, 0);
         nb = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
     }
-    const int need = (M + kBlock / 32 - 1) / (kBlock / 32);
+    const int need = (M + kBlock / 32 - 1) / (kBlock / 32);   // enough for one query per warp
     return need < nb ? need : nb;
 }
 

@@ -135,6 +135,25 @@ __device__ __forceinline__ bool search_query(const Index &ix, const float4 *src,
     return ok;
 }
 
+// Two queries per warp (halfwarp_nn): lanes 0-15 search query i, lanes 16-31
+// query i + 1 (when `live`); lane 0 of each half stores its correspondence.
+// Returns false on a search-stack overflow.
+template <int PREC>
+__device__ __forceinline__ bool search_pair(const Index &ix, const float4 *src, int *prev, const StepHead &h, int i,
+                                            bool live, bool p2p, int *stk_half) {
+    NNLane q;
+    if (live) {
+        start_query<PREC>(ix, src, prev, h, i, p2p, q);
+    } else {
+        const float z[3] = {0.0f, 0.0f, 0.0f};
+        nn_init(q, z, z);
+    }
+    const bool ok = halfwarp_nn<PREC>(ix, q, stk_half, live && q.best_j >= 0 ? q.best_j / kLeaf : -1, live);
+    if (live && (threadIdx.x & 15) == 0) prev[i] = (!ok || q.best_j < 0) ? 0 : q.best_j;
+    __syncwarp();
+    return ok;
+}
+
 // Point i's share of the pass sums at this pass's correspondence:
 // Welsch weight and energy term (Eq. 10, Eq. 12, Eq. 16); point-to-point: the
 // weighted centroids and cross-covariance terms; point-to-plane: g z z^T, g z h
