@@ -314,3 +314,34 @@ def test_workload2_full_size_properties(fr):
     tr = r["trace"]
     assert len(tr) == r["iterations"]
     assert int((np.diff(tr) > 0).sum()) <= r["stages"] - 1
+
+
+def test_workload3_full_size_properties(fr):
+    """Full-size workload 3 (Welsch point-to-plane, N = 500,000, M = 200,000):
+    sampled closest points at the final transform and one full-size pass
+    against the oracle (energy and xi*). Alg. 2's accepted energy is not
+    monotone as Alg. 1's is: when no line-search trial beats E_prev the best
+    trial is kept (the listing's rule), so a rise inside a stage needs a line
+    search, and there are at most as many rises as trials plus stage changes."""
+    pair = synth.config_pair(3)
+    t = fr.target_create(pair.Q, pair.normals)
+    r = fr.register(t, pair.P, params=fr.params_default("p2pl_welsch"), trace_capacity=100000)
+    assert r["status"] == "OK"
+    T = np.eye(4)
+    T[:3, :3], T[:3, 3] = r["R"], r["t"]
+    sel = np.random.default_rng(13).choice(pair.M, 3000, replace=False)
+    idx, d2 = fr.closest_points(t, _dev(pair.P), T)
+    io, do, dso = oracle.closest(oracle.apply(T, pair.P[sel].astype(float)), pair.Q.astype(float))
+    assert_nn_parity(idx.cpu().numpy()[sel], d2.cpu().numpy()[sel], io, do, dso)
+    nz = oracle.Normalization(c=r["center"], s=r["scale"])
+    Tn = np.eye(4)
+    Tn[:3, :3] = r["R"]
+    Tn[:3, 3] = nz.s * (r["R"] @ nz.c + r["t"] - nz.c)
+    out = fr.eval_pass(t, pair.P, "p2pl_welsch", Tn, nu=r["nu_min"], scale=nz.s, center=nz.c)
+    E, xs, _ = oracle_pass_p2pl(pair.P, pair.Q, pair.normals, Tn, r["nu_min"], nz.s, nz.c)
+    assert abs(out[0] - E) <= 1e-10 * max(1.0, abs(E))
+    assert np.abs(out[1:7] - xs).max() <= 1e-8
+    tr = r["trace"]
+    assert len(tr) == r["iterations"]
+    assert int((np.diff(tr) > 0).sum()) <= r["stages"] - 1 + r["line_search_trials"]
+    t.destroy()
