@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_accum_batch(const Slot *__restric
             else
                 last = accum_tile<1, PREC_FP64>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
                                                 red, &s_last);
-            if (last) finish_pass<kSumsP2PL>(h, sl.st, sl.partial, sl.ntiles, sl.resid, sl.trace, sS);
+            if (last) finish_pass<kSumsP2PL>(h, sl.st, sl.partial, sl.ntiles, sl.resid, sl.trace, sS, red);
         } else {
             bool last;
             if (h.prec == PREC_FP32)
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_accum_batch(const Slot *__restric
             else
                 last = accum_tile<0, PREC_FP64>(h, sl.st, sl.ix, sl.src, sl.prev, sl.resid, sl.partial, lt, sl.ntiles,
                                                 red, &s_last);
-            if (last) finish_pass<kSumsP2P>(h, sl.st, sl.partial, sl.ntiles, sl.resid, sl.trace, sS);
+            if (last) finish_pass<kSumsP2P>(h, sl.st, sl.partial, sl.ntiles, sl.resid, sl.trace, sS, red);
         }
         __syncthreads();   // s_tile and h are rewritten next round
     }

@@ -249,13 +249,15 @@ inline fricp_status setup_pair(const TargetDev &t, const fricp_params &prm, int6
     *h = initial_state(prm, m, ntiles, *scale, c, nu_min, trace_cap);
     double T0n[12];
     to_normalised(T0, *scale, c, T0n);
+    std::vector<double> sh(kTeamScratch);
+    const Team tm{sh.data()};   // the solver's algebra, as a team of one lane
     if (fricp::variant_p2pl(prm.variant)) {
-        se3_log(T0n, h->xk);
-        request_eval_xi(h, h->xk, 1);
+        log_state_T(tm, T0n, h->xk);
+        request_eval_xi(tm, h, h->xk, 1);
     } else {
         copy_n(h->Tk, T0n, 12);
-        se3_log(h->Tk, h->logTk);
-        request_eval_T(h, h->Tk, 1);
+        log_state_T(tm, h->Tk, h->logTk);
+        request_eval_state_T(tm, h, h->Tk, 1);
     }
     if (robust) {
         h->phase = PH_INIT;
@@ -270,10 +272,13 @@ inline fricp_status setup_pair(const TargetDev &t, const fricp_params &prm, int6
 inline void fill_result(const PairState &r, int variant, double scale, const double c[3], int trace_cap,
                         fricp_result *out) {
     double Tn[12];
-    if (fricp::variant_p2pl(variant))
-        se3_exp(r.xk, Tn);
-    else
+    if (fricp::variant_p2pl(variant)) {
+        std::vector<double> sh(kTeamScratch);
+        se3_exp(Team{sh.data()}, r.xk, sh.data(), sh.data() + 12);
+        copy_n(Tn, sh.data(), 12);
+    } else {
         copy_n(Tn, r.Tk, 12);
+    }
     to_caller(Tn, scale, c, out->R, out->t);
     out->status = r.status;
     out->iterations = r.iterations;

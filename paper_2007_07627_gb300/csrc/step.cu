@@ -7,7 +7,7 @@
 //            and each point's share of the alignment sums in FP64; each block
 //            reduces its tile into one record (fixed shared-memory tree, no
 //            atomics); the last block reduces all records in a fixed order and
-//            runs solver_step() on one thread, so the iteration never leaves
+//            runs solver_step() on one warp, so the iteration never leaves
 //            the device.
 #include "step_common.cuh"
 
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_accum(StepArgs a) {
     __syncthreads();
     if (h.done) return;
     if (accum_tile<VAR, PREC>(h, a.st, a.ix, a.src, a.prev, a.resid, a.partial, blockIdx.x, gridDim.x, red, &s_last))
-        finish_pass<K>(h, a.st, a.partial, gridDim.x, a.resid, a.trace, sS);
+        finish_pass<K>(h, a.st, a.partial, gridDim.x, a.resid, a.trace, sS, red);
 }
 
 // Correspondence step alone: index (original order) and FP64 squared distance.
@@ -88,19 +88,24 @@ __global__ void __launch_bounds__(128) k_closest(Index ix, const float *__restri
     }
 }
 
-// Single-evaluation set-up for fricp_eval_pass: T is normalised (R, t).
-__global__ void k_setup_eval(PairState *st, const double *T) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Single-evaluation set-up for fricp_eval_pass: T is normalised (R, t). One warp.
+__global__ void __launch_bounds__(32) k_setup_eval(PairState *gst, const double *T) {
+    __shared__ double sh[kTeamScratch];
+    const Team tm{sh};
+    PairState own = *gst;
+    PairState *st = &own;
     double Tn[12];
     for (int i = 0; i < 12; ++i) Tn[i] = T[i];
     if (fricp::variant_p2pl(st->variant)) {
         double xi[6];
-        se3_log(Tn, xi);
-        request_eval_xi(st, xi, 1);
+        log_state_T(tm, Tn, xi);
+        request_eval_xi(tm, st, xi, 1);
     } else {
-        request_eval_T(st, Tn, 1);
+        request_eval_state_T(tm, st, Tn, 1);
     }
     st->phase = PH_EVAL;
+    tm.sync();
+    if (tm.lane() == 0) *gst = own;
 }
 
 }  // namespace

@@ -297,11 +297,12 @@ __device__ __forceinline__ bool accum_tile(const StepHead &h, PairState *st, con
 }
 
 // Work of the block that completed a pass: the fixed-order reduction of the
-// tile records, then either the nu_max median (PH_INIT) or one solver step.
-// Resets the tile counter for the next pass.
+// tile records, then either the nu_max median (PH_INIT) or one solver step by
+// the block's first warp (team scratch: `team_sh`, kTeamScratch doubles of
+// shared memory free at this point). Resets the tile counter for the next pass.
 template <int K>
 __device__ __forceinline__ void finish_pass(const StepHead &h, PairState *st, const double *partial, int ntiles,
-                                            const double *resid, double *trace, double *sS) {
+                                            const double *resid, double *trace, double *sS, double *team_sh) {
     reduce_tiles<K>(partial, ntiles, sS);
     if (h.phase == PH_INIT) {
         const int n = h.M;
@@ -312,8 +313,8 @@ __device__ __forceinline__ void finish_pass(const StepHead &h, PairState *st, co
             if (st->eval_counts) st->corr_passes++;
             start_after_init(st, 0.5 * (lo + hi));
         }
-    } else if (threadIdx.x == 0) {
-        solver_step(st, sS, trace);
+    } else if (threadIdx.x < 32) {
+        solver_step(Team{team_sh}, st, sS, trace);
     }
     if (threadIdx.x == 0) st->counter = 0u;
     __syncthreads();

@@ -128,6 +128,34 @@ def test_chol6_matches_numpy(H):
     assert H.h_chol6_solve(_p(A), _p(b), _p(x)) == 0
 
 
+def test_chol6_zero_directions_are_the_reduced_system(H):
+    """Points in a plane: the directions with an all-zero row, column and
+    right-hand side get x_j = 0 and the rest solves the reduced system."""
+    g = np.random.default_rng(6)
+    keep = np.array([2, 3, 4])
+    B = g.standard_normal((3, 3))
+    A = np.zeros((6, 6))
+    A[np.ix_(keep, keep)] = B @ B.T + 0.1 * np.eye(3)
+    b = np.zeros(6)
+    b[keep] = g.standard_normal(3)
+    x = np.full(6, np.nan)
+    assert H.h_chol6_solve(_p(A), _p(b), _p(x)) == 1
+    ref = np.zeros(6)
+    ref[keep] = np.linalg.solve(A[np.ix_(keep, keep)], b[keep])
+    assert np.abs(x - ref).max() < 1e-12 and (x[[0, 1, 5]] == 0.0).all()
+    assert H.h_chol6_solve(_p(np.zeros((6, 6))), _p(np.zeros(6)), _p(x)) == 0
+    b[0] = 1.0                                   # a zero row with a nonzero right-hand side is singular
+    assert H.h_chol6_solve(_p(A), _p(b), _p(x)) == 0
+
+
+def test_procrustes_rotation_rejects_non_finite(H):
+    Hm = np.eye(3)
+    R = np.zeros(9)
+    for bad in (np.nan, np.inf):
+        Hm[1, 2] = bad
+        assert H.h_procrustes_rotation(_p(Hm), _p(R)) == 0
+
+
 @pytest.mark.parametrize("scale", [1.0, 0.2, 1e-4, 1e-8, 0.0])
 def test_chain_matrix_reproduces_appendix_d_gradient(H, scale):
     """J_i = K z_i with z_i = [R p_i x n_i; n_i] equals the oracle's App. D gradient."""
