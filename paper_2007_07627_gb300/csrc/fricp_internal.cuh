@@ -115,6 +115,11 @@ struct PairState {
     // transform the next pass applies to the source, caller units: x = Re p + te
     double Re[9];
     double te[3];
+    // derived from Re, te and nu for the search and per-point kernels (set_head_cache):
+    // float splits hi + lo of Re and te, 1 / (2 nu^2) and the Welsch cap radius^2 in caller units
+    float hRh[9], hRl[9], hth[3], htl[3];
+    float hcut2;
+    double hinv2nu2;
     // Anderson history, oldest first: G^(k-j), F^(k-j)
     double Gh[kMaxM + 1][6];
     double Fh[kMaxM + 1][6];

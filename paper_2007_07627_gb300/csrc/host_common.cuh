@@ -265,6 +265,7 @@ inline fricp_status setup_pair(const TargetDev &t, const fricp_params &prm, int6
         h->phase = PH_STAGE_START;
         h->nu = h->nu_max = h->nu_min = 1.0;
     }
+    set_head_cache_serial(h);
     return FRICP_OK;
 }
 

@@ -25,6 +25,13 @@
 
 namespace fricp {
 
+// Lanes of a device team: the first kTeamLanes lanes of a warp.
+#ifndef FRICP_TEAM_LANES
+#define FRICP_TEAM_LANES 32
+#endif
+constexpr int kTeamLanes = FRICP_TEAM_LANES;
+constexpr unsigned kTeamMask = kTeamLanes == 32 ? 0xffffffffu : ((1u << kTeamLanes) - 1u);
+
 struct Team {
     double *sh;   // scratch shared by the team: kTeamScratch doubles
     FRICP_HD int lane() const {
@@ -36,14 +43,14 @@ struct Team {
     }
     FRICP_HD int size() const {
 #ifdef __CUDA_ARCH__
-        return 32;
+        return kTeamLanes;
 #else
         return 1;
 #endif
     }
     FRICP_HD void sync() const {
 #ifdef __CUDA_ARCH__
-        __syncwarp();
+        __syncwarp(kTeamMask);
 #endif
     }
 };
@@ -193,7 +200,9 @@ FRICP_HD inline void se3_log(const Team &tm, const double *T, double xi[6], doub
     double R[9];
     t_load(T, R);
     const double v0 = 0.5 * (R[7] - R[5]), v1 = 0.5 * (R[2] - R[6]), v2 = 0.5 * (R[3] - R[1]);
-    const double sn = sqrt(fma(v2, v2, fma(v1, v1, v0 * v0)));
+    const double sn2 = fma(v2, v2, fma(v1, v1, v0 * v0));
+    const double isn = sn2 > 0.0 ? rsqrt64(sn2) : 0.0;   // 1 / sin th (unused when sin th = 0)
+    const double sn = sn2 * isn;
     const double cs = 0.5 * (R[0] + R[4] + R[8] - 1.0);
     const double th = atan2(sn, cs);
     const double th2 = th * th;
@@ -224,7 +233,7 @@ FRICP_HD inline void se3_log(const Team &tm, const double *T, double xi[6], doub
         const double nk = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
         for (int j = 0; j < 3; ++j) wv[j] = sg * th * k[j] / nk;
     } else {
-        const double f = th * rcp64(sn);
+        const double f = th * isn;
         wv[0] = f * v0; wv[1] = f * v1; wv[2] = f * v2;
     }
     double e;
@@ -444,10 +453,10 @@ FRICP_HD inline bool anderson_lstsq(const Team &tm, double *Dm, int mk, double t
         const double alpha = -copysign(nrm, v[j]);
         Rd[j] = alpha;
         if (nrm == 0.0) continue;
+        // v = x - alpha e_j has |v_j| = |x_j| + nrm, so v.v = 2 (nrm^2 + |x_j| nrm)
+        const double vv2 = fma(fabs(v[j]), nrm, nrm2);
         v[j] -= alpha;
-        const double vv = dot6(v, v);
-        if (vv == 0.0) continue;
-        const double ivv2 = 2.0 * rcp64(vv);
+        const double ivv2 = rcp64(vv2);   // 2 / v.v
         tm.sync();   // every lane has read column j
         for (int c = j + 1 + tm.lane(); c <= kMaxM; c += tm.size()) {
             if (c >= mk && c != kMaxM) continue;

@@ -32,6 +32,45 @@ FRICP_HD inline void copy_n(double *dst, const double *src, int n) {
     for (int i = 0; i < n; ++i) dst[i] = src[i];
 }
 
+// What every block of the next pass derives from Re, te and nu, computed once
+// where they change instead of in each block: the float splits hi + lo of Re and
+// te (the double-float transform of the search), 1 / (2 nu^2), and the Welsch cap
+// radius^2 in caller units, (d_n / s)^2 with d_n^2 / (2 nu^2) = kWelschCut.
+FRICP_HD inline void head_scalars(PairState *st) {
+    st->hinv2nu2 = st->nu > 0.0 ? 1.0 / (2.0 * st->nu * st->nu) : 0.0;
+    const double cut2 = st->nu > 0.0 ? kWelschCut * 2.0 * st->nu * st->nu / (st->s * st->s) : 0.0;
+    st->hcut2 = (cut2 > 0.0 && cut2 < 3.0e38) ? (float)(cut2 * (1.0 + 1e-5)) : INFINITY;
+}
+
+FRICP_HD inline void set_head_cache_serial(PairState *st) {
+    for (int i = 0; i < 9; ++i) split_double(st->Re[i], st->hRh[i], st->hRl[i]);
+    for (int r = 0; r < 3; ++r) split_double(st->te[r], st->hth[r], st->htl[r]);
+    head_scalars(st);
+}
+
+// The same by a team: one split per lane, exchanged through the scratch.
+FRICP_HD inline void set_head_cache(const Team &tm, PairState *st) {
+    float *f = reinterpret_cast<float *>(tm.sh + kShW);   // 24 floats
+    tm.sync();
+    for (int e = tm.lane(); e < 12; e += tm.size()) {
+        float h, l;
+        split_double(e < 9 ? st->Re[e] : st->te[e - 9], h, l);
+        f[e] = h;
+        f[12 + e] = l;
+    }
+    tm.sync();
+    for (int i = 0; i < 9; ++i) {
+        st->hRh[i] = f[i];
+        st->hRl[i] = f[12 + i];
+    }
+    for (int r = 0; r < 3; ++r) {
+        st->hth[r] = f[9 + r];
+        st->htl[r] = f[21 + r];
+    }
+    head_scalars(st);
+    tm.sync();
+}
+
 // Next pass evaluates the normalised transform T (scratch: R row-major, t):
 // the pass works in caller units, x = R p + t_o with t_o = t / s + c - R c.
 FRICP_HD inline void request_eval_T(const Team &tm, PairState *st, const double *T, int counts) {
@@ -458,12 +497,37 @@ static __device__ __noinline__ void start_after_init(PairState *st, double media
     st->cap = st->cap_first;
     st->phase = PH_STAGE_START;
     st->eval_counts = 0;   // the stage-start pass re-uses the correspondences at T0
+    head_scalars(st);
 }
 
-// One solver step by the 32 lanes of a warp (tm.sh: kTeamScratch doubles of
-// shared memory). S: the reduced sums of the pass just evaluated.
+// Each lane's own copy of the state: coalesced loads by the team into the
+// scratch, then every lane copies the scratch. Back: word k by lane k mod size.
+constexpr int kStateWords = (int)(sizeof(PairState) / sizeof(double));
+static_assert(sizeof(PairState) % sizeof(double) == 0 && kShW + kStateWords <= kTeamScratch, "state copy");
+
+__device__ inline void load_state(const Team &tm, const PairState *g, PairState *own) {
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(g);
+    unsigned long long *buf = reinterpret_cast<unsigned long long *>(tm.sh + kShW);
+    tm.sync();
+    for (int k = tm.lane(); k < kStateWords; k += tm.size()) buf[k] = src[k];
+    tm.sync();
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(own);
+    for (int k = 0; k < kStateWords; ++k) dst[k] = buf[k];
+    tm.sync();
+}
+
+__device__ inline void store_state(const Team &tm, const PairState *own, PairState *g) {
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(own);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(g);
+    for (int k = tm.lane(); k < kStateWords; k += tm.size()) dst[k] = src[k];
+}
+
+// One solver step by a team (the first kTeamLanes lanes of a warp; tm.sh:
+// kTeamScratch doubles of shared memory). S: the reduced sums of the pass just
+// evaluated.
 static __device__ __noinline__ void solver_step(Team tm, PairState *gst, const double *S, double *trace) {
-    PairState own = *gst;
+    PairState own;
+    load_state(tm, gst, &own);
     PairState *st = &own;
     st->device_steps++;
     if (st->eval_counts) st->corr_passes++;
@@ -490,8 +554,9 @@ static __device__ __noinline__ void solver_step(Team tm, PairState *gst, const d
     } else {
         p2p_step(tm, st, S, trace);
     }
-    tm.sync();
-    if (tm.lane() == 0) *gst = own;
+    set_head_cache(tm, st);
+    st->counter = 0u;   // the next pass's tile tickets start over
+    store_state(tm, st, gst);
 }
 
 }  // namespace fricp

@@ -91,8 +91,10 @@ __global__ void __launch_bounds__(128) k_closest(Index ix, const float *__restri
 // Single-evaluation set-up for fricp_eval_pass: T is normalised (R, t). One warp.
 __global__ void __launch_bounds__(32) k_setup_eval(PairState *gst, const double *T) {
     __shared__ double sh[kTeamScratch];
+    if (threadIdx.x >= kTeamLanes) return;
     const Team tm{sh};
-    PairState own = *gst;
+    PairState own;
+    load_state(tm, gst, &own);
     PairState *st = &own;
     double Tn[12];
     for (int i = 0; i < 12; ++i) Tn[i] = T[i];
@@ -104,8 +106,8 @@ __global__ void __launch_bounds__(32) k_setup_eval(PairState *gst, const double 
         request_eval_state_T(tm, st, Tn, 1);
     }
     st->phase = PH_EVAL;
-    tm.sync();
-    if (tm.lane() == 0) *gst = own;
+    set_head_cache(tm, st);
+    store_state(tm, st, gst);
 }
 
 }  // namespace

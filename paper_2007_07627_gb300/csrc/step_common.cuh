@@ -45,17 +45,33 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[K], double *out
     __syncthreads();   // `red` may be reused right away
 }
 
-// Fixed-order reduction of the tile records: warp w owns columns w, w+8, ...;
-// lane l sums rows l, l+32, ... and a shuffle tree finishes the column.
+// Fixed-order reduction of the tile records: thread t < G K (G = kBlock / K row
+// groups) sums column t mod K over rows g, g + G, g + 2 G, ... (g = t / K) in
+// order, eight loads in flight; the G partial sums of a column are then added
+// in group order. `red` holds kBlock doubles of shared memory.
 template <int K>
-__device__ __forceinline__ void reduce_tiles(const double *partial, int ntiles, double *S) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = wid; k < K; k += kBlock / 32) {
+__device__ __forceinline__ void reduce_tiles(const double *partial, int ntiles, double *S, double *red) {
+    constexpr int G = kBlock / K;
+    const int t = threadIdx.x;
+    if (t < G * K) {
+        const int k = t % K, g = t / K;
         double v = 0.0;
-        for (int r = lane; r < ntiles; r += 32) v += __ldcg(partial + (size_t)r * K + k);
+        int r = g;
+        for (; r + G * 7 < ntiles; r += G * 8) {
+            double x[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) S[k] = v;
+            for (int u = 0; u < 8; ++u) x[u] = __ldcg(partial + (size_t)(r + G * u) * K + k);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v += x[u];
+        }
+        for (; r < ntiles; r += G) v += __ldcg(partial + (size_t)r * K + k);
+        red[t] = v;
+    }
+    __syncthreads();
+    if (t < K) {
+        double v = red[t];
+        for (int g = 1; g < G; ++g) v += red[g * K + t];
+        S[t] = v;
     }
     __syncthreads();
 }
@@ -82,12 +98,16 @@ __device__ __forceinline__ void load_head(const PairState *st, StepHead &h) {
         h.c[r] = st->c[r];
     }
     h.scale = st->s;
-    h.inv2nu2 = st->nu > 0.0 ? 1.0 / (2.0 * st->nu * st->nu) : 0.0;
-    for (int i = 0; i < 9; ++i) split_double(h.R[i], h.Rh[i], h.Rl[i]);
-    for (int r = 0; r < 3; ++r) split_double(h.t[r], h.th[r], h.tl[r]);
-    // Welsch cap radius in caller units: (d_n / s)^2 with d_n^2 / (2 nu^2) = kWelschCut
-    const double cut2 = st->nu > 0.0 ? kWelschCut * 2.0 * st->nu * st->nu / (st->s * st->s) : 0.0;
-    h.cut2 = (cut2 > 0.0 && cut2 < 3.0e38) ? (float)(cut2 * (1.0 + 1e-5)) : __int_as_float(0x7f800000);
+    h.inv2nu2 = st->hinv2nu2;   // the derived values were set with Re, te and nu (set_head_cache)
+    for (int i = 0; i < 9; ++i) {
+        h.Rh[i] = st->hRh[i];
+        h.Rl[i] = st->hRl[i];
+    }
+    for (int r = 0; r < 3; ++r) {
+        h.th[r] = st->hth[r];
+        h.tl[r] = st->htl[r];
+    }
+    h.cut2 = st->hcut2;
 }
 
 __device__ __forceinline__ void transform_point(const StepHead &h, float4 p, double x[3]) {
@@ -303,7 +323,7 @@ __device__ __forceinline__ bool accum_tile(const StepHead &h, PairState *st, con
 template <int K>
 __device__ __forceinline__ void finish_pass(const StepHead &h, PairState *st, const double *partial, int ntiles,
                                             const double *resid, double *trace, double *sS, double *team_sh) {
-    reduce_tiles<K>(partial, ntiles, sS);
+    reduce_tiles<K>(partial, ntiles, sS, team_sh);
     if (h.phase == PH_INIT) {
         const int n = h.M;
         double lo, hi;
@@ -312,11 +332,11 @@ __device__ __forceinline__ void finish_pass(const StepHead &h, PairState *st, co
             st->device_steps++;
             if (st->eval_counts) st->corr_passes++;
             start_after_init(st, 0.5 * (lo + hi));
+            st->counter = 0u;   // the next pass's tile tickets start over
         }
-    } else if (threadIdx.x < 32) {
-        solver_step(Team{team_sh}, st, sS, trace);
+    } else if (threadIdx.x < kTeamLanes) {
+        solver_step(Team{team_sh}, st, sS, trace);   // resets the tickets in its copy of the state
     }
-    if (threadIdx.x == 0) st->counter = 0u;
     __syncthreads();
 }
 
