@@ -120,6 +120,7 @@ struct PairState {
     float hRh[9], hRl[9], hth[3], htl[3];
     float hcut2;
     double hinv2nu2;
+    double hnu;   // nu that hinv2nu2 and hcut2 belong to (0: not set)
     // Anderson history, oldest first: G^(k-j), F^(k-j)
     double Gh[kMaxM + 1][6];
     double Fh[kMaxM + 1][6];

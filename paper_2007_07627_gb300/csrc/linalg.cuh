@@ -240,9 +240,9 @@ FRICP_HD inline void se3_log(const Team &tm, const double *T, double xi[6], doub
     if (th < 1e-2) {
         e = 1.0 / 12.0 + th2 * (1.0 / 720.0) + th2 * th2 * (1.0 / 30240.0);
     } else {
-        double st, ct;
-        sincos(th, &st, &ct);
-        e = (1.0 - th * st * rcp64(2.0 * (1.0 - ct))) * rcp64(th2);
+        // sin th and cos th are sn and cs themselves (R orthogonal): no sincos
+        const double omc2 = 2.0 * (1.0 - cs);
+        e = (omc2 - th * sn) * rcp64(omc2 * th2);
     }
     double *W = w, *W2 = w + 9, *V = w + 18, *u = w + 27;
     double Wr[9];

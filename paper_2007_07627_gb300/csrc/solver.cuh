@@ -37,6 +37,8 @@ FRICP_HD inline void copy_n(double *dst, const double *src, int n) {
 // te (the double-float transform of the search), 1 / (2 nu^2), and the Welsch cap
 // radius^2 in caller units, (d_n / s)^2 with d_n^2 / (2 nu^2) = kWelschCut.
 FRICP_HD inline void head_scalars(PairState *st) {
+    if (st->hnu == st->nu && st->nu > 0.0) return;   // nu changes only at a stage boundary
+    st->hnu = st->nu;
     st->hinv2nu2 = st->nu > 0.0 ? 1.0 / (2.0 * st->nu * st->nu) : 0.0;
     const double cut2 = st->nu > 0.0 ? kWelschCut * 2.0 * st->nu * st->nu / (st->s * st->s) : 0.0;
     st->hcut2 = (cut2 > 0.0 && cut2 < 3.0e38) ? (float)(cut2 * (1.0 + 1e-5)) : INFINITY;
