@@ -202,11 +202,20 @@ fricp_status fricp_batch_register(int32_t npairs, const fricp_target *const *tar
                                   const double *T0, const fricp_params *params, void *stream,
                                   fricp_result *out, double *trace, int32_t trace_capacity);
 
+/* Fix the launch shape of later batched and served runs on every thread
+ * instead of autotuning it: chunk queries per search ticket (a divisor of 256),
+ * search blocks per SM (clamped to the kernel's occupancy) and the ticket
+ * order (1: fixed stride, 0: atomic counter). chunk = 0 returns to autotuning.
+ * The results do not depend on the shape, only the time. Errors: EINVAL. */
+fricp_status fricp_batch_set_shape(int32_t chunk, int32_t search_blocks_per_sm, int32_t static_order);
+
 /* Launch shape the autotuner chose for the last batched or served run on any
  * thread: queries per search ticket, search blocks per SM, accumulate blocks
- * per SM. Any pointer may be NULL. Never fails. */
+ * per SM, and static_order = 1 when the search tickets are dealt in a fixed
+ * stride (0: taken from an atomic counter). Any pointer may be NULL. Never
+ * fails. */
 void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_per_sm,
-                            int32_t *accumulate_blocks_per_sm);
+                            int32_t *accumulate_blocks_per_sm, int32_t *static_order);
 
 /* Serving loop with continuous batching (no counterpart in the paper).
  * Registrations are submitted at any time; fricp_server_step admits queued

@@ -95,7 +95,8 @@ def lib() -> ctypes.CDLL:
     pp = ctypes.POINTER(vp)
     L.fricp_batch_register.argtypes = [i32, pp, pp, ctypes.POINTER(i64), i32, dp, ctypes.POINTER(Params), vp,
                                        ctypes.POINTER(Result), dp, i32]
-    L.fricp_batch_last_shape.argtypes = [ctypes.POINTER(i32)] * 3
+    L.fricp_batch_last_shape.argtypes = [ctypes.POINTER(i32)] * 4
+    L.fricp_batch_set_shape.argtypes = [i32, i32, i32]
     L.fricp_estimate_normals.argtypes = [vp, i64, i32, i32, dp, vp, vp]
     L.fricp_server_create.argtypes = [ctypes.c_size_t, i32, i32, i32, vp, ctypes.POINTER(vp)]
     L.fricp_server_submit.argtypes = [vp, vp, vp, i64, i32, dp, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)]
@@ -106,7 +107,7 @@ def lib() -> ctypes.CDLL:
     for name in ("fricp_params_default", "fricp_target_create", "fricp_target_destroy", "fricp_register",
                  "fricp_closest_points", "fricp_eval_pass", "fricp_target_nu_min", "fricp_batch_register",
                  "fricp_server_create", "fricp_server_submit", "fricp_server_step", "fricp_server_poll",
-                 "fricp_server_destroy", "fricp_estimate_normals"):
+                 "fricp_server_destroy", "fricp_estimate_normals", "fricp_batch_set_shape"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -277,10 +278,16 @@ def batch_register(targets, sources, params=None, T0=None, stream=None, trace_ca
     return out
 
 
+def batch_set_shape(chunk: int = 0, search_blocks_per_sm: int = 1, static_order: bool = False) -> None:
+    """fricp_batch_set_shape: fix the batched launch shape (chunk = 0: autotune again)."""
+    _check(lib().fricp_batch_set_shape(chunk, search_blocks_per_sm, 1 if static_order else 0))
+
+
 def batch_last_shape() -> dict:
-    c, a, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    lib().fricp_batch_last_shape(ctypes.byref(c), ctypes.byref(a), ctypes.byref(b))
-    return {"chunk": c.value, "search_blocks_per_sm": a.value, "accumulate_blocks_per_sm": b.value}
+    c, a, b, o = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    lib().fricp_batch_last_shape(ctypes.byref(c), ctypes.byref(a), ctypes.byref(b), ctypes.byref(o))
+    return {"chunk": c.value, "search_blocks_per_sm": a.value, "accumulate_blocks_per_sm": b.value,
+            "static_order": bool(o.value)}
 
 
 def estimate_normals(q, k: int = 30, viewpoint=None, stream=None):

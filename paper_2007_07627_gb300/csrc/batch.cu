@@ -3,9 +3,11 @@
 // per set of launches:
 //   k_plan         one block: the list of tiles of the registrations that are
 //                  not done, and each one's step head (load_head);
-//   k_nn_batch     persistent warps take tickets of `chunk` queries from an
-//                  atomic counter over that list, so uneven registrations
-//                  share the GPU evenly; each query is searched by a warp;
+//   k_nn_batch     persistent warps take tickets of `chunk` queries over that
+//                  list, from an atomic counter (uneven registrations share
+//                  the GPU evenly) or dealt in a fixed stride (no atomics, the
+//                  warps in flight on one window of the list), whichever the
+//                  autotuner timed faster; each query is searched by a warp;
 //   k_accum_batch  persistent blocks take tiles from a second counter; the
 //                  block that completes a registration's pass reduces its tile
 //                  records and runs its solver step, so the single-thread
@@ -140,7 +142,7 @@ __device__ __forceinline__ void copy_head(const StepHead *src, StepHead *dst, in
 __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ slots, const StepHead *heads,
                                                      const int *__restrict__ tile_slot,
                                                      const int *__restrict__ tile_local, BatchCtl *ctl, int chunk,
-                                                     unsigned max_tickets) {
+                                                     unsigned max_tickets, int static_order) {
     __shared__ int s_stk[kBlock / 32][kWarpStack];
     __shared__ StepHead s_head[kBlock / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -149,10 +151,17 @@ __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ sl
     const int per_tile = kBlock / chunk;
     const unsigned total = min((unsigned)__ldcg(&ctl->n_tiles) * (unsigned)per_tile, max_tickets);
     int cur = -1;
+    unsigned next = blockIdx.x * (kBlock / 32) + w;   // fixed stride: this warp's tickets
+    const unsigned nwarps = gridDim.x * (kBlock / 32);
     for (;;) {
         unsigned tk = 0;
-        if (lane == 0) tk = atomicAdd(&ctl->nn_next, 1u);
-        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (static_order) {
+            tk = next;
+            next += nwarps;
+        } else {
+            if (lane == 0) tk = atomicAdd(&ctl->nn_next, 1u);
+            tk = __shfl_sync(0xffffffffu, tk, 0);
+        }
         if (tk >= total) break;
         const int tile = (int)(tk / per_tile), sub = (int)(tk % per_tile);
         const int p = __ldg(tile_slot + tile), lt = __ldg(tile_local + tile);
@@ -250,6 +259,7 @@ struct BatchShape {
     int chunk;        // queries per search ticket (divides kBlock)
     int nn_per_sm;    // search blocks per SM
     int acc_per_sm;   // accumulate blocks per SM
+    int static_order; // search tickets dealt in a fixed stride instead of an atomic counter
 };
 
 int sm_count() {
@@ -273,7 +283,8 @@ int max_per_sm(const void *kernel) {
 // number of registrations in flight rounded to a power of two).
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, BatchShape> g_tuned;
-BatchShape g_last_shape{1, 0, 0};
+BatchShape g_last_shape{1, 0, 0, 0};
+BatchShape g_forced{0, 0, 0, 0};   // chunk > 0: the shape fricp_batch_set_shape fixed
 
 std::pair<int, int> size_class(int64_t points, int nslots) {
     int a = 0, b = 0;
@@ -358,7 +369,7 @@ class BatchEngine {
     void launch_step(cudaStream_t st) {
         launch_plan(st);
         k_nn_batch<<<nn_blocks(), kBlock, 0, st>>>(d_slots, d_heads, d_tile_slot, d_tile_local, d_ctl, shape.chunk,
-                                                    0xffffffffu);
+                                                    0xffffffffu, shape.static_order);
         k_accum_batch<<<acc_blocks(), kBlock, 0, st>>>(d_slots, d_heads, d_tile_slot, d_tile_local, d_ctl);
         counters().launches += 3;
     }
@@ -402,11 +413,18 @@ class BatchEngine {
     // was; only the warm starts make the repeats cheaper, as in the steady
     // state. Small tickets balance the warps and keep the warps in flight on a
     // compact window of Morton-ordered queries (shared cache lines); large
-    // tickets take fewer atomics.
+    // tickets take fewer atomics; a fixed stride takes none.
     cudaError_t tune(int64_t points, int nslots) {
         const auto key = size_class(points, nslots);
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (g_forced.chunk > 0) {
+                shape = g_forced;
+                shape.nn_per_sm = std::min(std::max(shape.nn_per_sm, 1), max_per_sm((const void *)k_nn_batch));
+                shape.acc_per_sm = max_per_sm((const void *)k_accum_batch);
+                g_last_shape = shape;
+                return cudaSuccess;
+            }
             auto it = g_tuned.find(key);
             if (it != g_tuned.end()) {
                 shape = it->second;
@@ -421,23 +439,25 @@ class BatchEngine {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        const int chunks[] = {1, 2, 4, 8, 16};
+        // (chunk, static order): tickets from the counter, then fixed strides
+        const int cands[][2] = {{1, 0}, {2, 0}, {4, 0}, {8, 0}, {16, 0}, {1, 1}, {2, 1}};
         int per_sm[2] = {nn_max, (nn_max + 1) / 2};
-        BatchShape best{1, nn_max, acc_max};
+        BatchShape best{1, nn_max, acc_max, 0};
         float best_ms = 1e30f;
         cudaError_t e = cudaSuccess;
         // warm-up pass: sets the correspondences the timed repeats start from
         k_nn_batch<<<sm_count() * nn_max, kBlock, 0, s>>>(d_slots, d_heads, d_tile_slot, d_tile_local, d_ctl, 32,
-                                                          0xffffffffu);
+                                                          0xffffffffu, 0);
         counters().launches += 1;
-        for (int c : chunks) {
+        for (const auto &cd : cands) {
+            const int c = cd[0], so = cd[1];
             for (int pi = 0; pi < 2; ++pi) {
                 const int ps = per_sm[pi];
                 if (ps < 1 || ps > nn_max || (pi == 1 && ps == per_sm[0])) continue;
                 k_reset_nn_ticket<<<1, 1, 0, s>>>(d_ctl);
                 cudaEventRecord(e0, s);
                 k_nn_batch<<<sm_count() * ps, kBlock, 0, s>>>(d_slots, d_heads, d_tile_slot, d_tile_local, d_ctl, c,
-                                                              0xffffffffu);
+                                                              0xffffffffu, so);
                 cudaEventRecord(e1, s);
                 counters().launches += 2;
                 e = cudaEventSynchronize(e1);
@@ -446,7 +466,7 @@ class BatchEngine {
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (ms < best_ms) {
                     best_ms = ms;
-                    best = BatchShape{c, ps, acc_max};
+                    best = BatchShape{c, ps, acc_max, so};
                 }
             }
             if (e != cudaSuccess) break;
@@ -680,9 +700,19 @@ extern "C" fricp_status fricp_batch_register(int32_t npairs, const fricp_target 
     return rs;
 }
 
-extern "C" void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_per_sm,
-                                       int32_t *accumulate_blocks_per_sm) {
+extern "C" fricp_status fricp_batch_set_shape(int32_t chunk, int32_t search_blocks_per_sm, int32_t static_order) {
+    if (chunk != 0 && (chunk < 1 || chunk > fricp::kBlock || fricp::kBlock % chunk != 0 || search_blocks_per_sm < 1 ||
+                       (static_order != 0 && static_order != 1)))
+        return fricp::host::fail(FRICP_EINVAL, "batch shape: chunk must divide 256, blocks per SM >= 1, order 0 or 1");
     std::lock_guard<std::mutex> lk(fricp::g_tune_mu);
+    fricp::g_forced = fricp::BatchShape{chunk, search_blocks_per_sm, 0, static_order};
+    return FRICP_OK;
+}
+
+extern "C" void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_per_sm,
+                                       int32_t *accumulate_blocks_per_sm, int32_t *static_order) {
+    std::lock_guard<std::mutex> lk(fricp::g_tune_mu);
+    if (static_order) *static_order = fricp::g_last_shape.static_order;
     if (chunk) *chunk = fricp::g_last_shape.chunk;
     if (search_blocks_per_sm) *search_blocks_per_sm = fricp::g_last_shape.nn_per_sm;
     if (accumulate_blocks_per_sm) *accumulate_blocks_per_sm = fricp::g_last_shape.acc_per_sm;

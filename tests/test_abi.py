@@ -73,3 +73,11 @@ def test_defaults_and_argument_errors_without_gpu(libfricp):
     assert libfricp.fricp_target_create(None, None, 10, 0, None, ctypes.byref(out)) == 1
     assert b"NULL" in libfricp.fricp_last_error()
     assert libfricp.fricp_target_destroy(None) == 0
+
+
+def test_batch_shape_override_argument_checks(libfricp):
+    import paper_2007_07627_gb300 as fr
+    for bad in ((3, 1, 0), (512, 1, 0), (2, 0, 0), (2, 1, 2), (-1, 1, 0)):
+        assert libfricp.fricp_batch_set_shape(*bad) == 1   # FRICP_EINVAL
+    fr.batch_set_shape(4, 2, True)
+    fr.batch_set_shape(0)   # back to autotuning

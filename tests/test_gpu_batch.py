@@ -108,6 +108,26 @@ def test_single_pair_batch(fr):
     t.destroy()
 
 
+@pytest.mark.parametrize("chunk,static_order", [(1, True), (2, True), (4, False)])
+def test_forced_search_order_gives_the_same_results(fr, chunk, static_order):
+    """Search tickets dealt in a fixed stride or from the atomic counter, in any
+    size: every registration still equals its run alone."""
+    pairs = [synth.config_pair(1, 0.3), synth.config_pair(2, 0.02)]
+    variants = ("p2p", "p2p_welsch")
+    ts = [fr.target_create(p.Q, p.normals) for p in pairs]
+    prms = [_params(fr, v) for v in variants]
+    fr.batch_set_shape(chunk, 4, static_order)
+    try:
+        res = fr.batch_register(ts, [p.P for p in pairs], prms)
+        shape = fr.batch_last_shape()
+    finally:
+        fr.batch_set_shape(0)
+    assert shape["chunk"] == chunk and shape["static_order"] == static_order
+    for t, p, prm, r, v in zip(ts, pairs, prms, res, variants):
+        _assert_same(r, fr.register(t, p.P, params=prm), f"{v} chunk {chunk} static {static_order}")
+        t.destroy()
+
+
 def test_tiny_and_ragged_pairs(fr):
     g = np.random.default_rng(11)
     pairs = []
