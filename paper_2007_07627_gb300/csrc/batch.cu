@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ sl
     }
 }
 
-__global__ void __launch_bounds__(kBlock, 2) k_accum_batch(const Slot *__restrict__ slots, const StepHead *heads,
+__global__ void __launch_bounds__(kBlock, 3) k_accum_batch(const Slot *__restrict__ slots, const StepHead *heads,
                                                         const int *__restrict__ tile_slot,
                                                         const int *__restrict__ tile_local, BatchCtl *ctl) {
     __shared__ StepHead h;
