@@ -126,21 +126,22 @@ FRICP_HD inline void t_mul33(const Team &tm, const double *A, const double *B, d
 // Reciprocal and inverse square root from a float seed refined by two Newton
 // steps in FP64 (relative error ~1e-16): much shorter dependency chains than
 // the IEEE FP64 divide / square root on a GPU with few FP64 units. Arguments
-// outside the float range fall back to the IEEE operations.
+// outside the float range fall back to the IEEE operations. The steps are
+// written with explicit fma, so the host build rounds exactly as the device.
 FRICP_HD inline double rcp64(double a) {
     const double fa = fabs(a);
     if (!(fa > 1e-30 && fa < 1e30)) return 1.0 / a;
     double y = (double)(1.0f / (float)a);
-    y = y + y * (1.0 - a * y);
-    y = y + y * (1.0 - a * y);
+    y = fma(y, fma(-a, y, 1.0), y);
+    y = fma(y, fma(-a, y, 1.0), y);
     return y;
 }
 
 FRICP_HD inline double rsqrt64(double a) {
     if (!(a > 1e-30 && a < 1e30)) return 1.0 / sqrt(a);
     double y = (double)(1.0f / sqrtf((float)a));
-    y = y * (1.5 - 0.5 * a * y * y);
-    y = y * (1.5 - 0.5 * a * y * y);
+    y = y * fma(-0.5, (a * y) * y, 1.5);
+    y = y * fma(-0.5, (a * y) * y, 1.5);
     return y;
 }
 
