@@ -399,12 +399,23 @@ __device__ __forceinline__ void nn_thread(const Index &ix, NNLane &q, int start_
 //     compact the pushes: farther children below nearer ones);
 //   - the points of the popped buckets are spread over the lanes, two buckets
 //     per pass of 16 lanes each;
-// and the lexicographic (FP64 d^2, original index) minimum is then reduced
-// across the warp so every lane carries the same bound. Every point that can
-// beat the bound is examined, so the result is the same exact argmin as a
-// serial depth-first search.
+// and the float bound is then reduced across the warp so every lane prunes
+// with the same bound; the lexicographic (FP64 d^2, original index) minimum of
+// the lanes' winners is reduced once, at the end. Every point that can beat
+// the bound is examined, so the result is the same exact argmin as a serial
+// depth-first search.
 // ---------------------------------------------------------------------------
 constexpr int kWarpStack = 1024;  // per warp; a round grows the stack by <= 96
+
+// The float bound alone, min over the warp: what the pruning of the next round
+// needs. Each lane keeps the lexicographic winner of the candidates it was
+// offered; their minimum (warp_best) is taken once, when the search ends. The
+// candidates a lane accepts depend only on the bound, so the winner is the same
+// as with a full reduction every round.
+__device__ __forceinline__ void warp_min_bound(NNLane &q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q.bestf = fminf(q.bestf, __shfl_xor_sync(0xffffffffu, q.bestf, o));
+}
 
 __device__ __forceinline__ void warp_best(NNLane &q) {
 #pragma unroll
@@ -519,9 +530,10 @@ __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, in
                 if (j < ix.n) changed |= nn_offer<PREC>(q, target_point<PREC>(ix, j), j);
             }
         }
-        if (__ballot_sync(FULL, changed)) warp_best(q);   // only when some lane's bound moved
+        if (__ballot_sync(FULL, changed)) warp_min_bound(q);   // only when some lane's bound moved
         __syncwarp();
     }
+    warp_best(q);
     return true;
 }
 
@@ -536,6 +548,11 @@ __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, in
 // halves) if either stack would overflow.
 // ---------------------------------------------------------------------------
 constexpr int kHalfStack = kWarpStack / 2;
+
+__device__ __forceinline__ void half_min_bound(NNLane &q) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) q.bestf = fminf(q.bestf, __shfl_xor_sync(0xffffffffu, q.bestf, o));
+}
 
 __device__ __forceinline__ void half_best(NNLane &q) {
 #pragma unroll
@@ -651,9 +668,10 @@ __device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk
                 if (j < ix.n) changed |= nn_offer<PREC>(q, target_point<PREC>(ix, j), j);
             }
         }
-        if (__any_sync(FULL, changed)) half_best(q);
+        if (__any_sync(FULL, changed)) half_min_bound(q);
         __syncwarp();
     }
+    half_best(q);
     return true;
 }
 
