@@ -10,7 +10,7 @@
 //                  autotuner timed faster; each query is searched by a warp;
 //   k_accum_batch  persistent blocks take tiles from a second counter; the
 //                  block that completes a registration's pass reduces its tile
-//                  records and runs its solver step, so the single-thread
+//                  records and runs its solver step on one warp, so the
 //                  solvers of different registrations overlap with each other
 //                  and with the remaining tiles.
 // Per point and per tile the arithmetic and the reduction order are those of
