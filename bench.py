@@ -91,6 +91,18 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(xs, world, device="cuda"):
+    """Each value's maximum over the ranks (the slowest rank sets a replica run's
+    time); with one rank the values come back unchanged."""
+    if world == 1:
+        return [float(x) for x in xs]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in xs], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def workload_pair():
     from paper_2007_07627_gb300 import synth
     return synth.config_pair(2)
@@ -301,12 +313,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = fr.counters(reset=True)["kernel_launches"]
     clk = clocks.stop()
-    ms = statistics.mean(times)
+    (ms,) = max_over_ranks([statistics.mean(times)], world)
     if world > 1:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         torch.distributed.barrier()
-        ms = float(tt.item())
     it = statistics.mean(iters)
     value = world * pair.M * it / (ms / 1e3)
 
@@ -338,10 +347,13 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t0)
         th.destroy()
     cnt = fr.counters(reset=True)
-    e2e = {"value": world * pair.M * rh["iterations"] / statistics.mean(e2e_t), "unit": UNIT,
+    (e2e_s,) = max_over_ranks([statistics.mean(e2e_t)], world)
+    e2e = {"value": world * pair.M * rh["iterations"] / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": cnt["h2d_bytes"] // args.steps, "d2h_bytes_per_step": cnt["d2h_bytes"] // args.steps}
 
     if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
