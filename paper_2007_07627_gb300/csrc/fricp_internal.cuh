@@ -93,6 +93,7 @@ struct PairState {
     double c[3];       // normalisation centre (centroid of Q), caller units
     // ---- machine
     unsigned int counter;   // last-block ticket of the running step
+    unsigned int nn_next;   // next query pair of the search kernel (pair mode)
     int phase;
     int done;
     int status;

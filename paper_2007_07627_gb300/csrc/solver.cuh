@@ -557,7 +557,8 @@ static __device__ __noinline__ void solver_step(Team tm, PairState *gst, const d
         p2p_step(tm, st, S, trace);
     }
     set_head_cache(tm, st);
-    st->counter = 0u;   // the next pass's tile tickets start over
+    st->counter = 0u;   // the next pass's tile and search tickets start over
+    st->nn_next = 0u;
     store_state(tm, st, gst);
 }
 

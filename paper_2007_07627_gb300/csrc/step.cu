@@ -37,10 +37,16 @@ __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
                 a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
         }
     } else {
-        // similar work per query: two Morton-adjacent queries per warp, one per half
+        // similar work per query: two Morton-adjacent queries per warp, one per
+        // half; each warp takes the next pair from a counter in the state, so
+        // the SMs finish together (each pair's result depends only on the pair)
         int *stk = s_stk[threadIdx.x >> 5] + (threadIdx.x & 16 ? kHalfStack : 0);
-        for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); 2 * e < h.M; e += gridDim.x * wpb) {
-            const int i = 2 * e + ((threadIdx.x & 16) ? 1 : 0);
+        for (;;) {
+            unsigned e = 0;
+            if ((threadIdx.x & 31) == 0) e = atomicAdd(&a.st->nn_next, 1u);
+            e = __shfl_sync(0xffffffffu, e, 0);
+            if (2 * (long long)e >= h.M) break;
+            const int i = 2 * (int)e + ((threadIdx.x & 16) ? 1 : 0);
             if (!search_pair<PREC>(a.ix, a.src, a.prev, h, i, i < h.M, p2p, stk) && (threadIdx.x & 31) == 0)
                 a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
         }

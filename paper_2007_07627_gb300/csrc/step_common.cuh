@@ -332,7 +332,8 @@ __device__ __forceinline__ void finish_pass(const StepHead &h, PairState *st, co
             st->device_steps++;
             if (st->eval_counts) st->corr_passes++;
             start_after_init(st, 0.5 * (lo + hi));
-            st->counter = 0u;   // the next pass's tile tickets start over
+            st->counter = 0u;   // the next pass's tile and search tickets start over
+            st->nn_next = 0u;
         }
     } else if (threadIdx.x < kTeamLanes) {
         solver_step(Team{team_sh}, st, sS, trace);   // resets the tickets in its copy of the state
