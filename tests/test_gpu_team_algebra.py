@@ -11,7 +11,6 @@ import ctypes
 import os
 import shutil
 import subprocess
-import tempfile
 
 import numpy as np
 import pytest
@@ -27,7 +26,8 @@ def libs():
     import torch
     assert torch.cuda.is_available(), "GPU tests need CUDA"
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
-    d = tempfile.mkdtemp()
+    d = os.path.join(HERE, "_build")   # in-tree, git-ignored
+    os.makedirs(d, exist_ok=True)
     host = os.path.join(d, "liblinalg_host.so")
     dev = os.path.join(d, "liblinalg_device.so")
     subprocess.run([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-x", "cu",

@@ -6,7 +6,6 @@ import math
 import os
 import shutil
 import subprocess
-import tempfile
 
 import numpy as np
 import pytest
@@ -23,7 +22,8 @@ def H():
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
-    d = tempfile.mkdtemp()
+    d = os.path.join(HERE, "_build")   # in-tree, git-ignored
+    os.makedirs(d, exist_ok=True)
     so = os.path.join(d, "liblinalg_host.so")
     subprocess.run([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-x", "cu",
                     os.path.join(HERE, "linalg_host.cu"), "-o", so], check=True)
