@@ -28,7 +28,7 @@ def libs():
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     d = os.path.join(HERE, "_build")   # in-tree, git-ignored
     os.makedirs(d, exist_ok=True)
-    host = os.path.join(d, "liblinalg_host.so")
+    host = os.path.join(d, "liblinalg_host_team.so")   # its own file: another test may hold liblinalg_host.so
     dev = os.path.join(d, "liblinalg_device.so")
     subprocess.run([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-x", "cu",
                     os.path.join(HERE, "linalg_host.cu"), "-o", host], check=True)
