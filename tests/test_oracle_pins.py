@@ -540,3 +540,18 @@ def test_planar_registration_stays_in_the_plane(variant):
     assert r["t"][2] == 0.0
     # the copy to within the stopping rule (epsilon = 1e-5 on the change of the iterate)
     assert np.abs(r["R"] - Rz).max() < 5e-5 and np.abs(P @ r["R"].T + r["t"] - Q[:1200]).max() < 5e-5
+
+
+def test_line_search_first_trial_is_the_gauss_newton_step(monkeypatch):
+    """Alg. 2 with every AA step sabotaged: each rejected AA iterate starts the line
+    search along xi* - xi_prev at tau = 1, i.e. at the plain Gauss-Newton iterate
+    (Eq. 18 without AA), whose own energy check then runs the same way. So the
+    sabotaged run is plain Gauss-Newton: same iterations and accepted energies."""
+    P, Q, N, _, _ = _surface_pair(21, n=500, angle=0.5, noise=0.01)
+    prm = dict(variant="p2pl", max_iters=40)
+    plain = oracle.register(P, Q, oracle.Params(anderson_m=0, **prm), normals=N)
+    monkeypatch.setattr(oracle, "anderson_theta", lambda F, dF: np.full(dF.shape[1], 50.0))
+    bad = oracle.register(P, Q, oracle.Params(anderson_m=5, **prm), normals=N)
+    assert bad["aa_accepted"] == 0 and bad["iterations"] == plain["iterations"] > 3
+    assert bad["line_search_trials"] >= bad["reverts"] > plain["reverts"]
+    assert np.allclose(bad["trace"], plain["trace"], rtol=1e-10, atol=0)
