@@ -21,7 +21,8 @@ widened to float64:
 Where the paper is silent, garbled or inconsistent the reading taken is a named
 constant or a commented branch below, each citing the passage it reads.
 
-Pins (tests/test_oracle_*.py) tie every function here to something other than
+Pins (tests/test_oracle_pins.py, and tests/test_golden_parameters.py for the
+values the paper prints) tie every function here to something other than
 itself. The energy/iteration trajectory of a whole registration at workload
 scale is "parity unpinned" beyond these per-step pins: the paper prints no
 worked example and its datasets are not available.
