@@ -32,25 +32,40 @@ namespace fricp {
 constexpr int kTeamLanes = FRICP_TEAM_LANES;
 constexpr unsigned kTeamMask = kTeamLanes == 32 ? 0xffffffffu : ((1u << kTeamLanes) - 1u);
 
+// A host build that defines FRICP_HOST_TEAM (a CPU test) supplies the three
+// functions below and runs a team as host threads; every other host build is a
+// team of one lane.
+#if !defined(__CUDA_ARCH__) && defined(FRICP_HOST_TEAM)
+int fricp_host_team_lane();
+int fricp_host_team_size();
+void fricp_host_team_sync();
+#endif
+
 struct Team {
     double *sh;   // scratch shared by the team: kTeamScratch doubles
     FRICP_HD int lane() const {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__)
         return threadIdx.x & 31;
+#elif defined(FRICP_HOST_TEAM)
+        return fricp_host_team_lane();
 #else
         return 0;
 #endif
     }
     FRICP_HD int size() const {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__)
         return kTeamLanes;
+#elif defined(FRICP_HOST_TEAM)
+        return fricp_host_team_size();
 #else
         return 1;
 #endif
     }
     FRICP_HD void sync() const {
-#ifdef __CUDA_ARCH__
+#if defined(__CUDA_ARCH__)
         __syncwarp(kTeamMask);
+#elif defined(FRICP_HOST_TEAM)
+        fricp_host_team_sync();
 #endif
     }
 };
