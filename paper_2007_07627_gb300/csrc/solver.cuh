@@ -12,8 +12,9 @@
 // only appears through k - k_start, kept as n_body + 1.
 //
 // Every lane of the team runs the state machine on its own copy of the state
-// (so no lane ever reads a value another lane wrote to it); lane 0 writes its
-// copy back. Matrices shared between the lanes go through the team scratch.
+// (so no lane ever reads a value another lane wrote to it); the copies are
+// identical, and the lanes write them back word by word. Matrices shared
+// between the lanes go through the team scratch.
 #pragma once
 
 #include "fricp_internal.cuh"
