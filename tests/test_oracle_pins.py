@@ -300,6 +300,103 @@ def test_welsch_surrogate_majorizes():
 
 
 # --------------------------------------------------------------------------
+# Scale of Welsch's function (Eq. 10) fixed by App. C: nu_min is chosen by the
+# three-sigma rule, so nu is the standard deviation of the Gaussian weight
+# exp(-x^2 / (2 nu^2)) that Eq. 11 / Eq. 12 put on each residual. At one sigma
+# the weight is e^(-1/2); at three sigma e^(-9/2) (an outlier beyond 3 nu has
+# almost no weight, psi almost 1). A slip of nu^2 for 2 nu^2 (or the reverse)
+# gives e^(-1) and e^(-9), or e^(-1/4) and e^(-9/4).
+# --------------------------------------------------------------------------
+
+SIGMA1_W, SIGMA3_W = math.exp(-0.5), math.exp(-4.5)
+
+
+def test_welsch_function_is_one_minus_a_gaussian_of_sigma_nu():
+    for nu in (1e-3, 0.37, 5.0):
+        assert oracle.welsch(nu, nu) == pytest.approx(1.0 - SIGMA1_W, rel=1e-14)
+        assert oracle.welsch(3.0 * nu, nu) == pytest.approx(1.0 - SIGMA3_W, rel=1e-14)
+        assert oracle.welsch(-2.0 * nu, nu) == pytest.approx(1.0 - math.exp(-2.0), rel=1e-14)
+        assert oracle.welsch(0.0, nu) == 0.0
+    # three-sigma rule: a residual beyond 3 nu is treated as an outlier, psi > 0.98
+    assert oracle.welsch(3.0, 1.0) > 0.98
+
+
+def _two_height_pair(nu_n):
+    """A 10 x 10 grid of spacing 1 in the plane z = 0 (normals +z) and the same
+    grid lifted by heights that are nu and 3 nu in normalised units, in a
+    checkerboard. The closest point of each lifted point is the one below it
+    (heights < 1). Returns P, Q, normals and the lifted heights in normalised
+    units."""
+    gx = np.arange(10, dtype=np.float64)
+    X, Y = np.meshgrid(gx, gx)
+    Q = np.stack([X.ravel(), Y.ravel(), np.zeros(100)], 1)
+    lift = np.where((X.ravel() + Y.ravel()) % 2 == 0, 1.0, 3.0)
+    # the bounding-box diagonal of P u Q includes the largest lift: solve for it
+    diag = math.sqrt(2 * 81.0 / (1.0 - 9.0 * nu_n * nu_n))
+    P = Q.copy()
+    P[:, 2] = lift * nu_n * diag
+    P32, Q32 = P.astype(np.float32), Q.astype(np.float32)
+    nz = oracle.normalization(P32.astype(np.float64), Q32.astype(np.float64))
+    heights = nz.s * (P32[:, 2].astype(np.float64) - nz.c[2])
+    N = np.tile(np.array([0.0, 0.0, 1.0], np.float32), (100, 1))
+    return P32, Q32, N, lift, heights
+
+
+def test_weights_inside_algorithm_1_are_gaussian_of_sigma_nu(monkeypatch):
+    """The weights Alg. 1's alignment step (Eq. 12) receives at the start,
+    captured from the registration itself: e^(-1/2) at one sigma, e^(-9/2) at
+    three sigma."""
+    nu_n = 0.02
+    P, Q, _, lift, heights = _two_height_pair(nu_n)
+    assert np.allclose(heights, lift * nu_n, rtol=1e-6)
+    seen = []
+    real = oracle.weighted_procrustes
+
+    def spy(Pn, Qh, w):
+        seen.append(np.array(w))
+        return real(Pn, Qh, w)
+
+    monkeypatch.setattr(oracle, "weighted_procrustes", spy)
+    oracle.register(P, Q, oracle.Params(variant="p2p_welsch", nu_max=nu_n, nu_min=nu_n, max_iters=2))
+    w0 = seen[0]
+    assert np.allclose(w0[lift == 1.0], SIGMA1_W, rtol=1e-5)
+    assert np.allclose(w0[lift == 3.0], SIGMA3_W, rtol=1e-5)
+
+
+def test_weights_inside_algorithm_2_are_gaussian_of_sigma_nu(monkeypatch):
+    """The Gauss-Newton system of Eq. 18 that Alg. 2 factors at the start
+    (identity, normals +z): its u_z diagonal is sum gamma_i and its right-hand
+    side -sum gamma_i B_i, with gamma_i e^(-1/2) at one sigma and e^(-9/2) at
+    three sigma."""
+    nu_n = 0.02
+    P, Q, N, lift, heights = _two_height_pair(nu_n)
+    seen = []
+
+    class SlaSpy:
+        def __getattr__(self, name):
+            return getattr(sla, name)
+
+        def cho_factor(self, A, *a, **k):
+            seen.append(("A", np.array(A)))
+            return sla.cho_factor(A, *a, **k)
+
+        def cho_solve(self, cf, b, *a, **k):
+            seen.append(("b", np.array(b)))
+            return sla.cho_solve(cf, b, *a, **k)
+
+    monkeypatch.setattr(oracle, "sla", SlaSpy())
+    oracle.register(P, Q, oracle.Params(variant="p2pl_welsch", nu_max=nu_n, nu_min=nu_n), normals=N)
+    A = next(v for k, v in seen if k == "A")
+    b = next(v for k, v in seen if k == "b")
+    # planar target: delta_z, u_x and u_y change no distance, so the system is the
+    # (delta_x, delta_y, u_z) block, u_z last
+    assert A.shape == (3, 3)
+    n1, n3 = int((lift == 1.0).sum()), int((lift == 3.0).sum())
+    assert A[2, 2] == pytest.approx(n1 * SIGMA1_W + n3 * SIGMA3_W, rel=1e-5)
+    assert -b[2] == pytest.approx(nu_n * (n1 * SIGMA1_W + 3.0 * n3 * SIGMA3_W), rel=1e-5)
+
+
+# --------------------------------------------------------------------------
 # nu_min rationale (App. C): a planar square grid of spacing h gives E_Q = h.
 # --------------------------------------------------------------------------
 
