@@ -54,7 +54,9 @@ typedef enum {
     FRICP_EDEGENERATE = 5,  /* all Welsch weights vanished (sum w = 0) or the 6x6 point-to-plane
                                system is not positive definite; the last valid iterate is returned */
     FRICP_EUNSUPPORTED = 6, /* variant needs something the target lacks (normals) */
-    FRICP_EBUSY = 7         /* the server's request queue is full; step it and submit again */
+    FRICP_EBUSY = 7,        /* the server's request queue is full; step it and submit again */
+    FRICP_EOVERFLOW = 8     /* a bounded internal work buffer (a search stack, a candidate or tile
+                               list) overflowed; not expected on finite input */
 } fricp_status;
 
 typedef enum {
@@ -112,7 +114,7 @@ typedef struct {
 typedef struct {
     double  R[9];               /* row-major rotation */
     double  t[3];               /* translation */
-    int32_t status;             /* FRICP_OK or FRICP_EDEGENERATE */
+    int32_t status;             /* FRICP_OK, FRICP_EDEGENERATE or FRICP_EOVERFLOW */
     int32_t iterations;         /* inner-loop bodies run over all nu stages (Alg. 1 / Alg. 2) */
     int32_t corr_passes;        /* correspondence computations the algorithm needed */
     int32_t aa_accepted;        /* Anderson iterates that passed the energy check */

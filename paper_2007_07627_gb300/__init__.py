@@ -27,7 +27,7 @@ VARIANTS = {"p2p": P2P_AA, "p2p_welsch": P2P_WELSCH_AA, "p2pl_welsch": P2PL_WELS
 PREC_FP64, PREC_FP32, PREC_FP16_STORAGE = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp16": PREC_FP16_STORAGE}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EDEGENERATE", 6: "EUNSUPPORTED",
-          7: "EBUSY"}
+          7: "EBUSY", 8: "EOVERFLOW"}
 
 _PKG = pathlib.Path(__file__).resolve().parent
 _LIB_PATH = _PKG / "libfricp.so"

@@ -227,7 +227,7 @@ fricp_status fricp_estimate_normals(const float *q_xyz, int64_t n, int32_t k, in
     if (bad) return fail(FRICP_EINVAL, "q_xyz has NaN or Inf");
     if (e == cudaErrorMemoryAllocation) return fail(FRICP_ENOMEM, "device allocation for the normal estimate");
     if (e != cudaSuccess) return cuda_fail(e, "normal estimate");
-    if (overflow) return fail(FRICP_ECUDA, "neighbour search stack overflow");
+    if (overflow) return fail(FRICP_EOVERFLOW, "neighbour search stack overflow");
     return FRICP_OK;
 }
 
@@ -415,6 +415,7 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "evaluation pass");
     for (int i = 0; i < 48; ++i) out[i] = r.eval_out[i];
+    if (r.nn_overflow) return fail(FRICP_EOVERFLOW, "closest-point search stack overflow");
     if (r.status == FRICP_EDEGENERATE) return fail(FRICP_EDEGENERATE, "degenerate alignment problem");
     return FRICP_OK;
 }

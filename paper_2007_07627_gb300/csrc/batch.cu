@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ sl
                     ok = search_query<PREC_FP16>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
                 else
                     ok = search_query<PREC_FP64>(sl.ix, sl.src, sl.prev, h, i, p2p, stk);
-                if (!ok && lane == 0) sl.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+                if (!ok && lane == 0) sl.st->nn_overflow = 1;   // search-stack overflow: never expected
             }
         } else {   // two queries per warp, one per half
             int *hstk = stk + ((lane & 16) ? kHalfStack : 0);
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ sl
                     ok = search_pair<PREC_FP16>(sl.ix, sl.src, sl.prev, h, i, live, p2p, hstk);
                 else
                     ok = search_pair<PREC_FP64>(sl.ix, sl.src, sl.prev, h, i, live, p2p, hstk);
-                if (!ok && lane == 0) sl.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+                if (!ok && lane == 0) sl.st->nn_overflow = 1;   // search-stack overflow: never expected
             }
         }
     }
@@ -662,7 +662,7 @@ extern "C" fricp_status fricp_batch_register(int32_t npairs, const fricp_target 
             break;
         }
         if (eng.h_ctl->overflow) {
-            rs = fail(FRICP_ECUDA, "batched tile list overflow");
+            rs = fail(FRICP_EOVERFLOW, "batched tile list overflow");
             break;
         }
         if (eng.h_ctl->active == 0) break;
@@ -965,7 +965,7 @@ extern "C" fricp_status fricp_server_step(fricp_server *sv, int32_t nsteps, int3
                               std::chrono::duration<double>(sv->timeout_s));
     st = wait_event(sv->poll, deadline);
     if (st != FRICP_OK) return st;
-    if (sv->eng.h_ctl->overflow) return fail(FRICP_ECUDA, "served tile list overflow");
+    if (sv->eng.h_ctl->overflow) return fail(FRICP_EOVERFLOW, "served tile list overflow");
     if (graphs > 0) {   // the done flags describe the state after the launched steps
         st = harvest(sv);
         if (st != FRICP_OK) return st;

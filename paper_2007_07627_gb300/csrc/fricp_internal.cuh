@@ -97,6 +97,7 @@ struct PairState {
     int phase;
     int done;
     int status;
+    int nn_overflow;        // a search kernel ran out of its bounded stack (sticky; reported as FRICP_EOVERFLOW)
     int n_body;             // inner bodies run in this stage: k - k_start - 1
     int cap;                // current I_nu
     int eval_counts;        // the pending pass is a new correspondence computation

@@ -281,7 +281,7 @@ inline void fill_result(const PairState &r, int variant, double scale, const dou
         copy_n(Tn, r.Tk, 12);
     }
     to_caller(Tn, scale, c, out->R, out->t);
-    out->status = r.status;
+    out->status = r.nn_overflow ? FRICP_EOVERFLOW : r.status;
     out->iterations = r.iterations;
     out->corr_passes = r.corr_passes;
     out->aa_accepted = r.aa_accepted;

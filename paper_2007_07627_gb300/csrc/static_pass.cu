@@ -9,11 +9,11 @@
 // latency-critical loop where cudaMalloc / cudaFree would synchronize the
 // device, or a real-time or certified deployment that forbids allocation after
 // start-up.
+#include <atomic>
+#include <cmath>
 #include <cstring>
 
-#include "fricp_internal.cuh"
-#include "linalg.cuh"
-#include "solver.cuh"
+#include "host_common.cuh"
 
 namespace {
 
@@ -22,11 +22,12 @@ using fricp::PairState;
 constexpr int64_t kStaticMaxPoints = 32768;                        // largest m accepted
 constexpr int kStaticTiles = (int)(kStaticMaxPoints / fricp::kBlock);
 constexpr size_t kStateBytes = 16384;                               // >= sizeof(PairState)
-constexpr size_t kTBytes = 256;                                     // 12 doubles, padded
+constexpr size_t kTBytes = 256;                                     // 12 doubles, then the input flag
 constexpr size_t kPartialBytes = sizeof(double) * kStaticTiles * fricp::kMaxSums;
 constexpr size_t kPrevBytes = sizeof(int) * kStaticMaxPoints;
 constexpr size_t kSrcBytes = sizeof(float4) * kStaticMaxPoints;
 constexpr size_t kOffT = kStateBytes;
+constexpr size_t kOffFlag = kOffT + 128;                            // int: a source coordinate is NaN/Inf
 constexpr size_t kOffPartial = kOffT + kTBytes;
 constexpr size_t kOffPrev = kOffPartial + kPartialBytes;
 constexpr size_t kOffSrc = kOffPrev + kPrevBytes;
@@ -41,12 +42,22 @@ static_assert(kOffPartial % 256 == 0 && kOffPrev % 256 == 0 && kOffSrc % 256 == 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-char *g_addr[kMaxDevices];   // device address of g_scratch per device, set once
+// Device address of g_scratch per device, looked up by the first call on that
+// device. It belongs to that device's primary context: after cudaDeviceReset
+// the cached address is stale and must not be used, so a process that resets
+// a device must not call this entry point on that device again.
+std::atomic<char *> g_addr[kMaxDevices];
 
 // Source points in caller order as float4 (.w = index); no sort, no allocation.
-__global__ void k_pack_source(const float *__restrict__ p, int m, float4 *__restrict__ out) {
+// Sets *bad when a coordinate is NaN or Inf (the allocating pass rejects such
+// input the same way).
+__global__ void k_pack_source(const float *__restrict__ p, int m, float4 *__restrict__ out, int *bad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[i] = make_float4(p[3 * i], p[3 * i + 1], p[3 * i + 2], __int_as_float(i));
+    if (i < m) {
+        const float x = p[3 * i], y = p[3 * i + 1], z = p[3 * i + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(bad, 1);
+        out[i] = make_float4(x, y, z, __int_as_float(i));
+    }
 }
 
 fricp_status static_fail(fricp_status s, const char *msg) {
@@ -60,14 +71,16 @@ fricp_status scratch_address(char **out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return static_fail(FRICP_ECUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return static_fail(FRICP_EINVAL, "device index out of range");
-    if (g_addr[dev] == nullptr) {
+    char *addr = g_addr[dev].load(std::memory_order_acquire);
+    if (addr == nullptr) {   // concurrent first calls look up the same address
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_scratch);
         if (e != cudaSuccess || ptr == nullptr)
             return static_fail(FRICP_ECUDA, "cudaGetSymbolAddress(g_scratch) failed");
-        g_addr[dev] = (char *)ptr;
+        addr = (char *)ptr;
+        g_addr[dev].store(addr, std::memory_order_release);
     }
-    *out = g_addr[dev];
+    *out = addr;
     return FRICP_OK;
 }
 
@@ -93,26 +106,15 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
     double *T_dev = reinterpret_cast<double *>(base + kOffT);
     double *partial = reinterpret_cast<double *>(base + kOffPartial);
     int *prev = reinterpret_cast<int *>(base + kOffPrev);
+    int *bad_dev = reinterpret_cast<int *>(base + kOffFlag);
     float4 *src = reinterpret_cast<float4 *>(base + kOffSrc);
     const int ntiles = (int)((m + fricp::kBlock - 1) / fricp::kBlock);
 
-    // Host-side state image (the same initial state as fricp_eval_pass).
-    PairState h;
-    std::memset(&h, 0, sizeof(h));
-    h.variant = variant;
-    h.m = 5;
-    h.max_iters = 1000;
-    h.cap_first = 6;
-    h.cap_max = 10;
-    h.max_ls = 10;
-    h.M = (int)m;
-    h.ntiles = ntiles;
-    h.eps = 1e-5;
-    h.s = scale;
-    for (int a = 0; a < 3; ++a) h.c[a] = center ? center[a] : 0.0;
-    h.nu_min = 1.0;
-    h.E_prev = INFINITY;
-    h.cap = 6;
+    // Host-side state image: the same initial state as fricp_eval_pass.
+    fricp_params prm;
+    fricp_params_default(variant, &prm);
+    const double c[3] = {center ? center[0] : 0.0, center ? center[1] : 0.0, center ? center[2] : 0.0};
+    PairState h = fricp::host::initial_state(prm, m, ntiles, scale, c, 1.0, 0);
     h.nu = fricp::variant_robust(variant) ? nu : 1.0;
     double T12[12];
     for (int r = 0; r < 3; ++r) {
@@ -120,13 +122,15 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
         T12[9 + r] = T_normalized[4 * r + 3];
     }
     // Every region the pass reads is rewritten here, so nothing from the last
-    // call leaks in: the whole state (its last-block counter included), T, the correspondences (-1: none) and the packed source. Tile
+    // call leaks in: the whole state (its last-block counter included), T, the
+    // input flag, the correspondences (-1: none) and the packed source. Tile
     // records are written by the pass before they are read.
     cudaError_t e = cudaMemcpyAsync(st_dev, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(T_dev, T12, sizeof(T12), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad_dev, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(prev, 0xff, sizeof(int) * m, s);
     if (e == cudaSuccess) {
-        k_pack_source<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p_xyz_dev, (int)m, src);
+        k_pack_source<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p_xyz_dev, (int)m, src, bad_dev);
         fricp::counters().launches += 1;
         e = cudaGetLastError();
     }
@@ -141,11 +145,15 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
     a.trace = nullptr;
     if (e == cudaSuccess) e = fricp::launch_step(a, variant, fricp::PREC_FP64, ntiles, s);
     PairState r;
+    int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, st_dev, sizeof(r), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, bad_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return static_fail(FRICP_ECUDA, cudaGetErrorString(e));
     fricp::counters().h2d += sizeof(h) + sizeof(T12);
-    fricp::counters().d2h += sizeof(r);
+    fricp::counters().d2h += sizeof(r) + sizeof(int);
+    if (bad) return static_fail(FRICP_EINVAL, "p_xyz has NaN or Inf");
+    if (r.nn_overflow) return static_fail(FRICP_EOVERFLOW, "closest-point search stack overflow");
     for (int i = 0; i < 48; ++i) out[i] = r.eval_out[i];
     if (r.status == FRICP_EDEGENERATE) return static_fail(FRICP_EDEGENERATE, "degenerate alignment problem");
     return FRICP_OK;

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
         int *stk = s_stk[threadIdx.x >> 5];
         for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < h.M; i += gridDim.x * wpb) {
             if (!search_query<PREC>(a.ix, a.src, a.prev, h, i, p2p, stk) && (threadIdx.x & 31) == 0)
-                a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+                a.st->nn_overflow = 1;   // search-stack overflow: never expected
         }
     } else {
         // similar work per query: two Morton-adjacent queries per warp, one per
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
             if (2 * (long long)e >= h.M) break;
             const int i = 2 * (int)e + ((threadIdx.x & 16) ? 1 : 0);
             if (!search_pair<PREC>(a.ix, a.src, a.prev, h, i, i < h.M, p2p, stk) && (threadIdx.x & 31) == 0)
-                a.st->status = FRICP_ECUDA;   // search-stack overflow: never expected
+                a.st->nn_overflow = 1;   // search-stack overflow: never expected
         }
     }
 }

@@ -107,9 +107,24 @@ def test_single_pass_matches_oracle(fr, variant):
         nu = 0.02 + 0.1 * g.random()
         out = fr.eval_pass(t, P, variant, Tn, nu=nu, scale=nz.s, center=nz.c)
         if variant in ("p2pl_welsch", "p2pl"):
-            E, xs, _ = oracle_pass_p2pl(P, Q, pair.normals, Tn, nu, nz.s, nz.c, robust=variant == "p2pl_welsch")
+            robust = variant == "p2pl_welsch"
+            E, xs, xi = oracle_pass_p2pl(P, Q, pair.normals, Tn, nu, nz.s, nz.c, robust=robust)
             assert abs(out[0] - E) <= 1e-10 * max(1.0, abs(E))
             assert np.abs(out[1:7] - xs).max() <= 1e-9
+            # the 28 reduced sums (reduction step), in the ABI's convention:
+            # z = [y x n; n] with y = R p in normalised units (App. D, J = K z)
+            Pn, Qn = nz.fwd(P.astype(float)), nz.fwd(Q.astype(float))
+            Tx = oracle.se3_transform(xi)
+            X = oracle.apply(Tx, Pn)
+            idx, _, _ = oracle.closest(X, Qn)
+            nv = pair.normals.astype(float)[idx]
+            B = np.einsum("nd,nd->n", X - Qn[idx], nv)
+            gam = np.exp(-B * B / (2 * nu * nu)) if robust else np.ones_like(B)
+            z = np.concatenate([np.cross(Pn @ Tx[:3, :3].T, nv), nv], axis=1)
+            zz = (gam[:, None, None] * z[:, :, None] * z[:, None, :]).sum(0)
+            S = np.concatenate([zz[np.triu_indices(6)], (gam[:, None] * z * B[:, None]).sum(0),
+                                [oracle.welsch(B, nu).sum() if robust else (B * B).sum()]])
+            assert np.allclose(out[16:44], S, rtol=1e-11, atol=1e-12 * np.abs(S).max())
         else:
             E, Tp = oracle_pass_p2p(P, Q, Tn, nu, nz.s, nz.c, variant == "p2p_welsch")
             assert abs(out[0] - E) <= 1e-10 * max(1.0, abs(E))
