@@ -89,6 +89,26 @@ typedef enum {
     FRICP_PREC_FP16_STORAGE = 2
 } fricp_precision;
 
+/* How the exact closest-point search (Eq. 3) of fricp_register is laid out on
+ * the GPU; the result is the same exact argmin either way, only the time
+ * differs.
+ *   FRICP_SEARCH_TILE   a warp takes 8 Morton-adjacent queries (four lanes
+ *                       each), walks the tree once for all eight, pruning each
+ *                       node by every query's own bound, and streams the
+ *                       buckets kept through shared memory with asynchronous
+ *                       copies; a query without a warm start is searched by
+ *                       the whole warp alone. Fewer instructions per query,
+ *                       but one registration's slowest tiles bound the pass;
+ *   FRICP_SEARCH_QUERY  every query is searched by a whole warp (two per warp
+ *                       where the Welsch cap is off): the default, faster on a
+ *                       single registration.
+ * The batched and served engines choose between the two per size class by
+ * timing them (fricp_batch_last_shape). */
+typedef enum {
+    FRICP_SEARCH_TILE = 0,
+    FRICP_SEARCH_QUERY = 1
+} fricp_search;
+
 /* Solver parameters. fricp_params_default fills the paper's defaults. */
 typedef struct {
     int32_t variant;            /* fricp_variant */
@@ -107,7 +127,7 @@ typedef struct {
     int32_t max_steps;          /* hard cap on device steps (correspondence passes): 100000 */
     double  timeout_s;          /* host wait limit for one registration: 600 */
     int32_t precision;          /* fricp_precision: FRICP_PREC_FP64 */
-    int32_t pad0;
+    int32_t search;             /* fricp_search: FRICP_SEARCH_QUERY */
 } fricp_params;
 
 /* Result of one registration. All transforms in the caller's coordinates. */
@@ -207,15 +227,17 @@ fricp_status fricp_batch_register(int32_t npairs, const fricp_target *const *tar
 /* Fix the launch shape of later batched and served runs on every thread
  * instead of autotuning it: chunk queries per search ticket (a divisor of 256),
  * search blocks per SM (clamped to the kernel's occupancy) and the ticket
- * order (1: fixed stride, 0: atomic counter). chunk = 0 returns to autotuning.
- * The results do not depend on the shape, only the time. Errors: EINVAL. */
+ * order: 0 = from an atomic counter, one query per warp; 1 = dealt in a fixed
+ * stride, one query per warp; 2 = query tiles (tickets of 8 Morton-adjacent
+ * queries searched together by a warp, see FRICP_SEARCH_TILE; chunk is then
+ * 8). chunk = 0 returns to autotuning. The results do not depend on the shape,
+ * only the time. Errors: EINVAL. */
 fricp_status fricp_batch_set_shape(int32_t chunk, int32_t search_blocks_per_sm, int32_t static_order);
 
 /* Launch shape the autotuner chose for the last batched or served run on any
  * thread: queries per search ticket, search blocks per SM, accumulate blocks
- * per SM, and static_order = 1 when the search tickets are dealt in a fixed
- * stride (0: taken from an atomic counter). Any pointer may be NULL. Never
- * fails. */
+ * per SM, and the ticket order (0 counter, 1 fixed stride, 2 query tiles, as
+ * in fricp_batch_set_shape). Any pointer may be NULL. Never fails. */
 void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_per_sm,
                             int32_t *accumulate_blocks_per_sm, int32_t *static_order);
 

@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
         ("max_line_search", ctypes.c_int32), ("eps", ctypes.c_double), ("nu_max", ctypes.c_double),
         ("nu_min", ctypes.c_double), ("nu_min_floor", ctypes.c_double), ("steps_per_sync", ctypes.c_int32),
         ("use_graph", ctypes.c_int32), ("time_passes", ctypes.c_int32), ("max_steps", ctypes.c_int32),
-        ("timeout_s", ctypes.c_double), ("precision", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("timeout_s", ctypes.c_double), ("precision", ctypes.c_int32), ("search", ctypes.c_int32),
     ]
 
 
@@ -278,16 +278,17 @@ def batch_register(targets, sources, params=None, T0=None, stream=None, trace_ca
     return out
 
 
-def batch_set_shape(chunk: int = 0, search_blocks_per_sm: int = 1, static_order: bool = False) -> None:
-    """fricp_batch_set_shape: fix the batched launch shape (chunk = 0: autotune again)."""
-    _check(lib().fricp_batch_set_shape(chunk, search_blocks_per_sm, 1 if static_order else 0))
+def batch_set_shape(chunk: int = 0, search_blocks_per_sm: int = 1, static_order=0) -> None:
+    """fricp_batch_set_shape: fix the batched launch shape (chunk = 0: autotune again).
+    static_order: 0 counter, 1 fixed stride (True), 2 query tiles."""
+    _check(lib().fricp_batch_set_shape(chunk, search_blocks_per_sm, int(static_order)))
 
 
 def batch_last_shape() -> dict:
     c, a, b, o = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     lib().fricp_batch_last_shape(ctypes.byref(c), ctypes.byref(a), ctypes.byref(b), ctypes.byref(o))
     return {"chunk": c.value, "search_blocks_per_sm": a.value, "accumulate_blocks_per_sm": b.value,
-            "static_order": bool(o.value)}
+            "static_order": int(o.value)}
 
 
 def estimate_normals(q, k: int = 30, viewpoint=None, stream=None):

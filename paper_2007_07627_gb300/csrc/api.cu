@@ -57,7 +57,7 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
         const int64_t before = counters().launches;   // capture records launches, it does not run them
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int k = 0; k < chunk; ++k) fricp::launch_step(a, variant, prec, ntiles, s);
+            for (int k = 0; k < chunk; ++k) fricp::launch_step(a, variant, prec, ntiles, s, nullptr, prm.search);
             e = cudaStreamEndCapture(s, &graph.g);
         }
         counters().launches = before;
@@ -75,7 +75,7 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
         } else {
             for (int k = 0; k < chunk && e == cudaSuccess; ++k) {
                 if (timing) cudaEventRecord(tev[3 * k], s);
-                e = fricp::launch_step(a, variant, prec, ntiles, s, timing ? tev[3 * k + 1] : nullptr);
+                e = fricp::launch_step(a, variant, prec, ntiles, s, timing ? tev[3 * k + 1] : nullptr, prm.search);
                 if (timing) cudaEventRecord(tev[3 * k + 2], s);
             }
         }
@@ -157,6 +157,7 @@ fricp_status fricp_params_default(int32_t variant, fricp_params *out) {
     out->max_steps = 100000;
     out->timeout_s = 600.0;
     out->precision = FRICP_PREC_FP64;
+    out->search = FRICP_SEARCH_QUERY;
     return FRICP_OK;
 }
 
@@ -409,7 +410,7 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
     a.partial = partial.p;
     a.resid = nullptr;
     a.trace = nullptr;
-    if (e == cudaSuccess) e = fricp::launch_step(a, variant, fricp::PREC_FP64, ntiles, s);
+    if (e == cudaSuccess) e = fricp::launch_step(a, variant, fricp::PREC_FP64, ntiles, s, nullptr, FRICP_SEARCH_QUERY);   // a cold pass
     PairState r;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, st_dev.p, sizeof(r), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -7,7 +7,9 @@
 //                  list, from an atomic counter (uneven registrations share
 //                  the GPU evenly) or dealt in a fixed stride (no atomics, the
 //                  warps in flight on one window of the list), whichever the
-//                  autotuner timed faster; each query is searched by a warp;
+//                  autotuner timed faster; each query is searched by a warp,
+//                  or each ticket of kTileQ queries by a warp as one query
+//                  tile (search_tile);
 //   k_accum_batch  persistent blocks take tiles from a second counter; the
 //                  block that completes a registration's pass reduces its tile
 //                  records and runs its solver step on one warp, so the
@@ -56,6 +58,9 @@ struct BatchCtl {
 };
 
 constexpr int kPlanThreads = 1024;
+// Order of the search tickets (BatchShape::order): from an atomic counter, in a
+// fixed stride, or query tiles of kTileQ from the counter.
+constexpr int kOrderCounter = 0, kOrderStride = 1, kOrderTiles = 2;
 constexpr int kMaxSlots = 4096;
 constexpr int kSlotsPerThread = kMaxSlots / kPlanThreads;
 
@@ -142,12 +147,16 @@ __device__ __forceinline__ void copy_head(const StepHead *src, StepHead *dst, in
 __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ slots, const StepHead *heads,
                                                      const int *__restrict__ tile_slot,
                                                      const int *__restrict__ tile_local, BatchCtl *ctl, int chunk,
-                                                     unsigned max_tickets, int static_order) {
+                                                     unsigned max_tickets, int order) {
     __shared__ int s_stk[kBlock / 32][kWarpStack];
+    __shared__ __align__(16) float4 s_stage[kBlock / 32][kRing * 32];
     __shared__ StepHead s_head[kBlock / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *stk = s_stk[w];
     StepHead &h = s_head[w];
+    const bool tiles = order == kOrderTiles;
+    const int static_order = order == kOrderStride;
+    if (tiles) chunk = kTileQ;
     const int per_tile = kBlock / chunk;
     const unsigned total = min((unsigned)__ldcg(&ctl->n_tiles) * (unsigned)per_tile, max_tickets);
     int cur = -1;
@@ -175,7 +184,16 @@ __global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ sl
         const int i0 = lt * kBlock + sub * chunk;
         const int i1 = min(i0 + chunk, h.M);
         const bool p2p = !fricp::variant_p2pl(h.variant);
-        if (p2p && h.welsch && h.phase != PH_INIT) {   // Welsch cap active: one query per warp (as k_nn)
+        if (tiles) {   // the ticket's queries as one query tile
+            bool ok;
+            if (h.prec == PREC_FP32)
+                ok = search_tile<PREC_FP32>(sl.ix, sl.src, sl.prev, h, i0, i1, p2p, stk, s_stage[w]);
+            else if (h.prec == PREC_FP16)
+                ok = search_tile<PREC_FP16>(sl.ix, sl.src, sl.prev, h, i0, i1, p2p, stk, s_stage[w]);
+            else
+                ok = search_tile<PREC_FP64>(sl.ix, sl.src, sl.prev, h, i0, i1, p2p, stk, s_stage[w]);
+            if (!ok && lane == 0) sl.st->nn_overflow = 1;   // search-stack overflow: never expected
+        } else if (p2p && h.welsch && h.phase != PH_INIT) {   // Welsch cap active: one query per warp (as k_nn)
             for (int i = i0; i < i1; ++i) {
                 bool ok;
                 if (h.prec == PREC_FP32)
@@ -259,7 +277,7 @@ struct BatchShape {
     int chunk;        // queries per search ticket (divides kBlock)
     int nn_per_sm;    // search blocks per SM
     int acc_per_sm;   // accumulate blocks per SM
-    int static_order; // search tickets dealt in a fixed stride instead of an atomic counter
+    int order;        // kOrderCounter, kOrderStride or kOrderTiles
 };
 
 int sm_count() {
@@ -369,7 +387,7 @@ class BatchEngine {
     void launch_step(cudaStream_t st) {
         launch_plan(st);
         k_nn_batch<<<nn_blocks(), kBlock, 0, st>>>(d_slots, d_heads, d_tile_slot, d_tile_local, d_ctl, shape.chunk,
-                                                    0xffffffffu, shape.static_order);
+                                                    0xffffffffu, shape.order);
         k_accum_batch<<<acc_blocks(), kBlock, 0, st>>>(d_slots, d_heads, d_tile_slot, d_tile_local, d_ctl);
         counters().launches += 3;
     }
@@ -439,8 +457,9 @@ class BatchEngine {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        // (chunk, static order): tickets from the counter, then fixed strides
-        const int cands[][2] = {{1, 0}, {2, 0}, {4, 0}, {8, 0}, {16, 0}, {1, 1}, {2, 1}};
+        // (chunk, order): tickets from the counter, fixed strides, query tiles
+        const int cands[][2] = {{1, kOrderCounter}, {2, kOrderCounter}, {4, kOrderCounter}, {8, kOrderCounter},
+                                {16, kOrderCounter}, {1, kOrderStride}, {2, kOrderStride}, {kTileQ, kOrderTiles}};
         int per_sm[2] = {nn_max, (nn_max + 1) / 2};
         BatchShape best{1, nn_max, acc_max, 0};
         float best_ms = 1e30f;
@@ -702,17 +721,18 @@ extern "C" fricp_status fricp_batch_register(int32_t npairs, const fricp_target 
 
 extern "C" fricp_status fricp_batch_set_shape(int32_t chunk, int32_t search_blocks_per_sm, int32_t static_order) {
     if (chunk != 0 && (chunk < 1 || chunk > fricp::kBlock || fricp::kBlock % chunk != 0 || search_blocks_per_sm < 1 ||
-                       (static_order != 0 && static_order != 1)))
-        return fricp::host::fail(FRICP_EINVAL, "batch shape: chunk must divide 256, blocks per SM >= 1, order 0 or 1");
+                       static_order < fricp::kOrderCounter || static_order > fricp::kOrderTiles))
+        return fricp::host::fail(FRICP_EINVAL, "batch shape: chunk must divide 256, blocks per SM >= 1, order 0, 1 or 2");
     std::lock_guard<std::mutex> lk(fricp::g_tune_mu);
-    fricp::g_forced = fricp::BatchShape{chunk, search_blocks_per_sm, 0, static_order};
+    fricp::g_forced = fricp::BatchShape{static_order == fricp::kOrderTiles ? fricp::kTileQ : chunk,
+                                        search_blocks_per_sm, 0, static_order};
     return FRICP_OK;
 }
 
 extern "C" void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_per_sm,
                                        int32_t *accumulate_blocks_per_sm, int32_t *static_order) {
     std::lock_guard<std::mutex> lk(fricp::g_tune_mu);
-    if (static_order) *static_order = fricp::g_last_shape.static_order;
+    if (static_order) *static_order = fricp::g_last_shape.order;
     if (chunk) *chunk = fricp::g_last_shape.chunk;
     if (search_blocks_per_sm) *search_blocks_per_sm = fricp::g_last_shape.nn_per_sm;
     if (accumulate_blocks_per_sm) *accumulate_blocks_per_sm = fricp::g_last_shape.acc_per_sm;

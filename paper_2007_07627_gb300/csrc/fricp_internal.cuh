@@ -93,7 +93,7 @@ struct PairState {
     double c[3];       // normalisation centre (centroid of Q), caller units
     // ---- machine
     unsigned int counter;   // last-block ticket of the running step
-    unsigned int nn_next;   // next query pair of the search kernel (pair mode)
+    unsigned int nn_next;   // next work unit of the search kernel (query pair or query tile)
     int phase;
     int done;
     int status;
@@ -678,6 +678,252 @@ __device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk
 }
 
 // ---------------------------------------------------------------------------
+// Query tile: a warp holds kTileQ = 8 Morton-adjacent queries, each on a
+// group of four lanes (lane = 4 g + u: query g, sub-lane u; the four lanes of
+// a group carry the same query and the same warm start: the bound is the
+// distance to the previous pass's correspondence, or the Welsch cap).
+// Adjacent queries need mostly the same part of the tree, so the warp walks
+// it once for all eight:
+//   - from the bucket of one query's warm start, the siblings of that
+//     bucket's path to the root are tested (their subtrees partition the rest
+//     of the tree), then the children of every node kept, up to 32 nodes a
+//     round: sub-lane u tests the children of nodes u, u + 4, ... of the round
+//     against its own query's ball with the pruning test of the serial search,
+//     and a node is kept when it is within some query's bound;
+//   - the buckets kept are staged, two per pass, in shared memory (one
+//     coalesced 16-byte load per lane; FP16 storage is decoded here, once per
+//     point); sub-lane u offers staged points u, u + 4, ..., u + 28 to its
+//     query, and the group shares its float bound after every pass.
+// When the walk ends, the four sub-lanes' winners are reduced to the
+// lexicographic (FP64 distance, index) minimum. Every point that can beat a
+// query's bound lies in a bucket whose ancestors and itself passed that
+// query's test, and whichever sub-lane is offered the argmin keeps it (its
+// float distance is within the tie window of any bound), so the result is the
+// exact argmin of the serial search, ties included. A query far from the
+// others costs its own ball's nodes, not a box around everybody's.
+//
+// Queries without a warm start (the first pass) are set aside, and so is
+// every query of a tile whose walk would overflow its stack or bucket list
+// (not expected): the caller searches them one by one with the whole warp
+// (warp_nn). Returns the ballot mask of the lanes whose query is set aside (all
+// four lanes of a group); their state is undefined.
+//
+// Per warp: `stk` kTileStack ints and `pend` kTilePend ints (which warp_nn may
+// reuse as its stack afterwards: kTileStack + kTilePend <= kWarpStack), and
+// `stage` kRing x 32 float4.
+// ---------------------------------------------------------------------------
+constexpr int kTileQ = 8;             // queries per warp
+constexpr int kTileStack = 512;       // nodes kept and not yet expanded
+constexpr int kTileDrain = 16;        // buckets kept before they are scanned
+constexpr int kTilePend = kTileDrain + 64;   // a round adds <= 64, the path siblings <= 27
+static_assert(kTileStack + kTilePend <= kWarpStack, "tile buffers share the per-warp search stack");
+
+// Lexicographic winner and float bound of the four lanes of a group.
+__device__ __forceinline__ void group4_best(NNLane &q) {
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, q.best_hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, q.best_lo, o);
+        const int oo = __shfl_xor_sync(0xffffffffu, q.best_orig, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, q.best_j, o);
+        const float of = __shfl_xor_sync(0xffffffffu, q.bestf, o);
+        if (lex_less(oh, ol, oo, q.best_hi, q.best_lo, q.best_orig)) {
+            q.best_hi = oh;
+            q.best_lo = ol;
+            q.best_orig = oo;
+            q.best_j = oj;
+        }
+        q.bestf = fminf(q.bestf, of);
+    }
+}
+
+__device__ __forceinline__ bool ball_meets(const NNLane &q, bool easy, float4 lo, float4 hi) {
+    return easy && box_d2(lo, hi, q.xh, q.xl) * kShrink <= q.bestf;
+}
+
+// Asynchronous 16-byte global -> shared copies (cp.async, cached in L1).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kRing = 4;   // bucket pairs in flight in the scan (stage: kRing x 32 float4 per warp)
+
+// Scan the buckets pend[0 .. np), two per pass. FP32/FP64 storage: the pairs
+// stream through a ring of kRing stage slots with asynchronous copies, so
+// kRing - 1 pairs are in flight while one is offered; FP16 storage is decoded
+// by each lane on the way in.
+template <int PREC>
+__device__ __forceinline__ void tile_scan(const Index &ix, NNLane &q, bool easy, const int *pend, int np,
+                                          float4 *stage) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int u = lane & 3;
+    const float INF = __int_as_float(0x7f800000);
+    const int npairs = (np + 1) >> 1;
+    // pair k -> ring slot k % kRing: lane l brings point l & 15 of bucket 2k (l < 16) or 2k + 1
+    auto issue = [&](int k) {
+        if (k < npairs) {
+            const int mine = (lane < 16) ? pend[2 * k] : (2 * k + 1 < np ? pend[2 * k + 1] : -1);
+            const int jm = (mine - ix.L) * kLeaf + (lane & 15);
+            float4 *dst = stage + (k % kRing) * 32 + lane;
+            if (mine >= 0 && jm < ix.n) {
+                if (PREC == PREC_FP16)
+                    *dst = target_point<PREC>(ix, jm);
+                else
+                    cp_async16(dst, ix.pts + jm);
+            } else {
+                *dst = make_float4(INF, INF, INF, 0.0f);
+            }
+        }
+        cp_async_commit();   // one group per call, empty or not, so the counting below holds
+    };
+#pragma unroll
+    for (int k = 0; k < kRing - 1; ++k) issue(k);
+    for (int k = 0; k < npairs; ++k) {
+        issue(k + kRing - 1);          // into the slot consumed in the previous round
+        cp_async_wait<kRing - 1>();    // this lane's copy of pair k has landed
+        __syncwarp();                  // ... and every lane's
+        const float4 *sl = stage + (k % kRing) * 32;
+        if (easy) {
+            const int la = pend[2 * k];
+            const int lb = (2 * k + 1 < np) ? pend[2 * k + 1] : la;
+            const int ja = (la - ix.L) * kLeaf, jb = (lb - ix.L) * kLeaf;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) nn_offer<PREC>(q, sl[4 * t + u], ja + 4 * t + u);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) nn_offer<PREC>(q, sl[16 + 4 * t + u], jb + 4 * t + u);
+        }
+        // the group shares its float bound (the winners are reduced at the end)
+        q.bestf = fminf(q.bestf, __shfl_xor_sync(FULL, q.bestf, 1));
+        q.bestf = fminf(q.bestf, __shfl_xor_sync(FULL, q.bestf, 2));
+        __syncwarp();                  // slot k % kRing is free for pair k + kRing
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+// Append the nodes of `cand` (lanes t < nc hold one each) whose bit is set in
+// `keep`: buckets to pend, inner nodes to the stack. Returns false when either
+// would overflow.
+__device__ __forceinline__ bool tile_keep(const Index &ix, int cand, int nc, unsigned keep, int *stk, int &sp,
+                                          int *pend, int &np) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const bool kept = lane < nc && ((keep >> lane) & 1u);
+    const unsigned ml = __ballot_sync(FULL, kept && cand >= ix.L);
+    const unsigned mi = __ballot_sync(FULL, kept && cand < ix.L);
+    if (np + __popc(ml) > kTilePend || sp + __popc(mi) > kTileStack) return false;
+    if (kept && cand >= ix.L) pend[np + __popc(ml & below)] = cand;
+    if (kept && cand < ix.L) stk[sp + __popc(mi & below)] = cand;
+    np += __popc(ml);
+    sp += __popc(mi);
+    __syncwarp();
+    return true;
+}
+
+template <int PREC>
+__device__ __forceinline__ unsigned tile_nn(const Index &ix, NNLane &q, bool live, int *stk, int *pend,
+                                            float4 *stage) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int u = lane & 3;
+    const float INF = __int_as_float(0x7f800000);
+    const bool easy = live && q.best_j >= 0 && q.bestf < INF;
+    const unsigned emask = __ballot_sync(FULL, easy);
+    const unsigned cold = __ballot_sync(FULL, live && !easy);
+    if (emask == 0u) return cold;
+    int depth = 0;
+    while ((1 << depth) < ix.L) ++depth;
+    const int start = ix.L + __shfl_sync(FULL, q.best_j, __ffs(emask) - 1) / kLeaf;
+    int sp = 0, np = 0;
+    bool ok = true;
+    // the start bucket holds a warm-start point: it is within that query's bound
+    if (lane == 0) pend[0] = start;
+    np = 1;
+    // the siblings of the start bucket's path, root side first (so the deepest
+    // ends on top of the stack), in batches of eight
+    for (int k0 = 0; k0 < depth && ok; k0 += 8) {
+        int nd[2];
+        bool pass[2];
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int k = k0 + 4 * v + u;
+            nd[v] = k < depth ? (start >> (depth - 1 - k)) ^ 1 : 0;
+            pass[v] = nd[v] != 0 && ball_meets(q, easy, __ldg(ix.nodes + 2 * nd[v]), __ldg(ix.nodes + 2 * nd[v] + 1));
+        }
+        const unsigned m0 = __ballot_sync(FULL, pass[0]), m1 = __ballot_sync(FULL, pass[1]);
+        // lane t < 8 stands for sibling k0 + t (held by sub-lane t & 3 in slot t >> 2)
+        const int o0 = __shfl_sync(FULL, nd[0], lane & 3), o1 = __shfl_sync(FULL, nd[1], lane & 3);
+        const int cand = (lane >> 2) == 0 ? o0 : o1;
+        const unsigned keep = ((m0 & 0x11111111u) ? 1u : 0u) | ((m0 & 0x22222222u) ? 2u : 0u) |
+                              ((m0 & 0x44444444u) ? 4u : 0u) | ((m0 & 0x88888888u) ? 8u : 0u) |
+                              ((m1 & 0x11111111u) ? 16u : 0u) | ((m1 & 0x22222222u) ? 32u : 0u) |
+                              ((m1 & 0x44444444u) ? 64u : 0u) | ((m1 & 0x88888888u) ? 128u : 0u);
+        ok = tile_keep(ix, cand, min(8, depth - k0), keep, stk, sp, pend, np);
+    }
+    while (ok && (sp > 0 || np > 0)) {
+        if (np >= kTileDrain || (sp == 0 && np > 0)) {
+            tile_scan<PREC>(ix, q, easy, pend, np, stage);
+            np = 0;
+        }
+        if (sp == 0) break;
+        // pop up to 32 nodes; sub-lane u expands nodes u, u + 4, ..., u + 28
+        // (slot v holds node 4 v + u): a small walk uses the first slots only,
+        // a large one expands 32 nodes per round
+        const int k = min(32, sp);
+        const int nslot = (k + 3) >> 2;
+        int nd[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) nd[v] = (4 * v + u < k) ? stk[sp - 1 - (4 * v + u)] : 0;
+        sp -= k;
+        __syncwarp();
+        unsigned keep[2] = {0u, 0u};   // bit 2 (4 v + u') + c of word v >> 2: child c of node 4 v + u'
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            if (v < nslot) {
+                bool pass0 = false, pass1 = false;
+                if (nd[v] != 0) {
+                    const float4 *b = ix.nodes + 4 * nd[v];
+                    pass0 = ball_meets(q, easy, __ldg(b), __ldg(b + 1));
+                    pass1 = ball_meets(q, easy, __ldg(b + 2), __ldg(b + 3));
+                }
+                unsigned m0 = __ballot_sync(FULL, pass0), m1 = __ballot_sync(FULL, pass1);
+                // fold the eight groups: bit w of the low nibble = some query kept it
+                m0 |= m0 >> 16; m0 |= m0 >> 8; m0 |= m0 >> 4;
+                m1 |= m1 >> 16; m1 |= m1 >> 8; m1 |= m1 >> 4;
+                unsigned bits = 0u;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) bits |= (((m0 >> w) & 1u) << (2 * w)) | (((m1 >> w) & 1u) << (2 * w + 1));
+                keep[v >> 2] |= bits << (8 * (v & 3));
+            }
+        }
+        // lane t stands for child t & 1 of node (t >> 1) + 16 h (h: the word),
+        // held by sub-lane (t >> 1) & 3 in slot (t >> 3) + 4 h
+        const int src = (lane >> 1) & 3;
+#pragma unroll
+        for (int hw = 0; hw < 2; ++hw) {
+            if (16 * hw < k) {
+                int cand = 0;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int o = __shfl_sync(FULL, nd[4 * hw + v], src);
+                    if ((lane >> 3) == v) cand = 2 * o + (lane & 1);
+                }
+                ok = ok && tile_keep(ix, cand, min(32, 2 * (k - 16 * hw)), keep[hw], stk, sp, pend, np);
+            }
+        }
+    }
+    if (!ok) return __ballot_sync(FULL, live);
+    group4_best(q);
+    return cold;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (index.cu, step.cu). All return cudaError_t.
 // ---------------------------------------------------------------------------
 struct TargetDev {
@@ -718,10 +964,11 @@ cudaError_t prepare_source(const float *p_dev, int64_t m, cudaStream_t s, float4
                            float lo[3], float hi[3], int *bad_input);
 cudaError_t launch_closest(const TargetDev *t, const float *p_dev, int64_t m, const double T[12],
                            int64_t *idx, double *d2, cudaStream_t s);
-// One device step: the closest-point search kernel, then the accumulate/solve
+// One device step: the closest-point search kernel (query tiles, or one query
+// per warp for search == FRICP_SEARCH_QUERY), then the accumulate/solve
 // kernel. When `mid` is given it is recorded between the two.
 cudaError_t launch_step(const StepArgs &a, int variant, int prec, int ntiles, cudaStream_t s,
-                        cudaEvent_t mid = nullptr);
+                        cudaEvent_t mid = nullptr, int search = FRICP_SEARCH_QUERY);
 cudaError_t launch_setup_eval_xi(PairState *st, const double *T_normalized12, cudaStream_t s);
 
 }  // namespace fricp

@@ -76,6 +76,7 @@ inline fricp_status check_params(const fricp_params *p) {
     if (p->precision < FRICP_PREC_FP64 || p->precision > FRICP_PREC_FP16_STORAGE)
         return fail(FRICP_EINVAL, "unknown precision");
     if (!(p->timeout_s > 0.0)) return fail(FRICP_EINVAL, "timeout_s must be > 0");
+    if (p->search != FRICP_SEARCH_TILE && p->search != FRICP_SEARCH_QUERY) return fail(FRICP_EINVAL, "unknown search");
     return FRICP_OK;
 }
 

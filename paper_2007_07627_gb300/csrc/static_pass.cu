@@ -143,7 +143,7 @@ extern "C" fricp_status fricp_eval_pass_static(const fricp_target *target, const
     a.partial = partial;
     a.resid = nullptr;
     a.trace = nullptr;
-    if (e == cudaSuccess) e = fricp::launch_step(a, variant, fricp::PREC_FP64, ntiles, s);
+    if (e == cudaSuccess) e = fricp::launch_step(a, variant, fricp::PREC_FP64, ntiles, s, nullptr, FRICP_SEARCH_QUERY);   // a cold pass
     PairState r;
     int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, st_dev, sizeof(r), cudaMemcpyDeviceToHost, s);

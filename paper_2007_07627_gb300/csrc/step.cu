@@ -1,8 +1,9 @@
 // One device step = one correspondence pass of Alg. 1 / Alg. 2 plus the
 // decision that follows it, in two kernels:
-//   k_nn     double-float transform (Sec. 3, x = R p + t), warm start from the
+//   k_nn_tile double-float transform (Sec. 3, x = R p + t), warm start from the
 //            previous correspondence, exact closest target point (Eq. 3), one
-//            warp per query (warp_nn);
+//            warp per tile of kTileQ Morton-adjacent queries (tile_nn); k_nn,
+//            one warp per query (warp_nn), is the alternative search;
 //   k_accum  residual, Welsch weight and energy term (Eq. 10, Eq. 12, Eq. 16)
 //            and each point's share of the alignment sums in FP64; each block
 //            reduces its tile into one record (fixed shared-memory tree, no
@@ -50,6 +51,32 @@ __global__ void __launch_bounds__(kBlock) k_nn(StepArgs a) {
             if (!search_pair<PREC>(a.ix, a.src, a.prev, h, i, i < h.M, p2p, stk) && (threadIdx.x & 31) == 0)
                 a.st->nn_overflow = 1;   // search-stack overflow: never expected
         }
+    }
+}
+
+// Search kernel over query tiles: persistent warps take tiles of kTileQ
+// Morton-adjacent queries (four lanes per query, search_tile) from a counter
+// in the state (the tiles' costs vary with the surface and the outliers they
+// hold). Each result depends only on its query, so the order changes no bit.
+template <int PREC>
+__global__ void __launch_bounds__(kBlock) k_nn_tile(StepArgs a) {
+    __shared__ StepHead h;
+    __shared__ int s_buf[kBlock / 32][kWarpStack];
+    __shared__ __align__(16) float4 s_stage[kBlock / 32][kRing * 32];
+    if (threadIdx.x == 0) load_head(a.st, h);
+    __syncthreads();
+    if (h.done) return;
+    const bool p2p = !fricp::variant_p2pl(h.variant);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned e = 0;
+        if (lane == 0) e = atomicAdd(&a.st->nn_next, 1u);
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if ((long long)kTileQ * e >= h.M) break;
+        const int i0 = kTileQ * (int)e;
+        if (!search_tile<PREC>(a.ix, a.src, a.prev, h, i0, min(i0 + kTileQ, h.M), p2p, s_buf[w], s_stage[w]) &&
+            lane == 0)
+            a.st->nn_overflow = 1;   // search-stack overflow: never expected
     }
 }
 
@@ -118,25 +145,30 @@ __global__ void __launch_bounds__(32) k_setup_eval(PairState *gst, const double 
 
 }  // namespace
 
-// Blocks of the search kernel k_nn<PREC> (persistent warps): enough to fill
-// every SM at that kernel's occupancy, and no more than the queries need.
-template <int PREC>
-int nn_blocks(int M) {
-    static int nb = 0;
-    if (nb == 0) {
+// Blocks of a persistent search kernel: enough to fill every SM at that
+// kernel's occupancy, and no more than the work units need (M / per_warp
+// queries per warp).
+template <typename K>
+int persistent_blocks(K kernel, int *cache, int M, int per_warp) {
+    if (*cache == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nn<PREC>, kBlock, 0);
-        nb = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+        *cache = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
     }
-    const int need = (M + kBlock / 32 - 1) / (kBlock / 32);   // enough for one query per warp
-    return need < nb ? need : nb;
+    const int warps = (M + per_warp - 1) / per_warp;
+    const int need = (warps + kBlock / 32 - 1) / (kBlock / 32);
+    return need < *cache ? need : *cache;
 }
 
 template <int PREC>
-void launch_step_prec(const StepArgs &a, int variant, int ntiles, cudaStream_t s, cudaEvent_t mid) {
-    k_nn<PREC><<<nn_blocks<PREC>(ntiles * kBlock), kBlock, 0, s>>>(a);
+void launch_step_prec(const StepArgs &a, int variant, int ntiles, int search, cudaStream_t s, cudaEvent_t mid) {
+    static int nb_query = 0, nb_tile = 0;
+    if (search == FRICP_SEARCH_QUERY)
+        k_nn<PREC><<<persistent_blocks(k_nn<PREC>, &nb_query, ntiles * kBlock, 1), kBlock, 0, s>>>(a);
+    else
+        k_nn_tile<PREC><<<persistent_blocks(k_nn_tile<PREC>, &nb_tile, ntiles * kBlock, kTileQ), kBlock, 0, s>>>(a);
     if (mid) cudaEventRecord(mid, s);
     if (fricp::variant_p2pl(variant))
         k_accum<1, PREC><<<ntiles, kBlock, 0, s>>>(a);
@@ -144,13 +176,14 @@ void launch_step_prec(const StepArgs &a, int variant, int ntiles, cudaStream_t s
         k_accum<0, PREC><<<ntiles, kBlock, 0, s>>>(a);
 }
 
-cudaError_t launch_step(const StepArgs &a, int variant, int prec, int ntiles, cudaStream_t s, cudaEvent_t mid) {
+cudaError_t launch_step(const StepArgs &a, int variant, int prec, int ntiles, cudaStream_t s, cudaEvent_t mid,
+                        int search) {
     if (prec == PREC_FP32)
-        launch_step_prec<PREC_FP32>(a, variant, ntiles, s, mid);
+        launch_step_prec<PREC_FP32>(a, variant, ntiles, search, s, mid);
     else if (prec == PREC_FP16)
-        launch_step_prec<PREC_FP16>(a, variant, ntiles, s, mid);
+        launch_step_prec<PREC_FP16>(a, variant, ntiles, search, s, mid);
     else
-        launch_step_prec<PREC_FP64>(a, variant, ntiles, s, mid);
+        launch_step_prec<PREC_FP64>(a, variant, ntiles, search, s, mid);
     counters().launches += 2;
     return cudaGetLastError();
 }

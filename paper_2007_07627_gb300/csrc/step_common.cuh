@@ -174,6 +174,37 @@ __device__ __forceinline__ bool search_pair(const Index &ix, const float4 *src, 
     return ok;
 }
 
+// Queries i0 .. i0 + kTileQ - 1 (below i1) as one query tile (tile_nn); the
+// queries it sets aside (no warm start: the first pass) are then searched one
+// by one by the whole warp (warp_nn). The group head stores each
+// correspondence. `wbuf`: kWarpStack ints per warp; `stage`: kRing x 32
+// float4. Returns false on a search-stack overflow.
+template <int PREC>
+__device__ __forceinline__ bool search_tile(const Index &ix, const float4 *src, int *prev, const StepHead &h, int i0,
+                                            int i1, bool p2p, int *wbuf, float4 *stage) {
+    const int lane = threadIdx.x & 31;
+    const int i = i0 + (lane >> 2);
+    const bool live = i < i1;
+    NNLane q;
+    if (live) {
+        start_query<PREC>(ix, src, prev, h, i, p2p, q);
+    } else {
+        const float z[3] = {0.0f, 0.0f, 0.0f};
+        nn_init(q, z, z);
+    }
+    const unsigned aside = tile_nn<PREC>(ix, q, live, wbuf, wbuf + kTileStack, stage);
+    if (live && (lane & 3) == 0 && !((aside >> lane) & 1u)) prev[i] = q.best_j;   // warm-started: best_j >= 0
+    __syncwarp();
+    bool ok = true;
+    unsigned heads = aside & 0x11111111u;
+    while (heads) {
+        const int g = (__ffs(heads) - 1) >> 2;
+        heads &= heads - 1u;
+        ok = search_query<PREC>(ix, src, prev, h, i0 + g, p2p, wbuf) && ok;
+    }
+    return ok;
+}
+
 // Point i's share of the pass sums at this pass's correspondence:
 // Welsch weight and energy term (Eq. 10, Eq. 12, Eq. 16); point-to-point: the
 // weighted centroids and cross-covariance terms; point-to-plane: g z z^T, g z h

@@ -108,7 +108,7 @@ def test_single_pair_batch(fr):
     t.destroy()
 
 
-@pytest.mark.parametrize("chunk,static_order", [(1, True), (2, True), (4, False)])
+@pytest.mark.parametrize("chunk,static_order", [(1, True), (2, True), (4, False), (8, 2)])
 def test_forced_search_order_gives_the_same_results(fr, chunk, static_order):
     """Search tickets dealt in a fixed stride or from the atomic counter, in any
     size: every registration still equals its run alone."""
