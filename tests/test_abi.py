@@ -77,7 +77,8 @@ def test_defaults_and_argument_errors_without_gpu(libfricp):
 
 def test_batch_shape_override_argument_checks(libfricp):
     import paper_2007_07627_gb300 as fr
-    for bad in ((3, 1, 0), (512, 1, 0), (2, 0, 0), (2, 1, 2), (-1, 1, 0)):
+    for bad in ((3, 1, 0), (512, 1, 0), (2, 0, 0), (2, 1, 3), (2, 1, -1), (-1, 1, 0)):
         assert libfricp.fricp_batch_set_shape(*bad) == 1   # FRICP_EINVAL
     fr.batch_set_shape(4, 2, True)
+    fr.batch_set_shape(8, 2, 2)   # query tiles
     fr.batch_set_shape(0)   # back to autotuning
