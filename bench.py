@@ -1,12 +1,12 @@
 #!/usr/bin/env python3
 """Throughput of the registration hot path in correspondence queries per second.
 
-Workload: Welsch-robust point-to-point ICP with Anderson acceleration (m = 5) and
-the paper's nu schedule (Alg. 1), on a seeded sum-of-Gaussian-bumps height field:
-N = 100,000 target points, M = 80,000 source points cropped to 60% overlap, noise
-0.005 x diagonal, 10% uniform outliers, random rigid motion (angle <= 25 deg,
-translation <= 0.1 x diagonal), identity start. Synthetic inputs stand in for the
-paper's scans.
+Headline workload: Welsch-robust point-to-plane ICP with Anderson acceleration
+(Alg. 2) on a seeded union of 8 random ellipsoids with analytic normals:
+N = 500,000 target points, M = 200,000 source points cropped to 50% overlap,
+noise 0.003 x diagonal, 5% uniform outliers, random rigid motion (angle <= 25
+deg, translation <= 0.1 x diagonal), identity start. Synthetic inputs stand in
+for the paper's scans.
 
 One step = one whole registration through the C ABI: target index build and
 nu_min statistic, source preparation, the nu_max pass, and every fused
@@ -18,27 +18,23 @@ N > 1 runs independent replicas, one per rank (weak scaling), launched by
 torch.distributed.run. --impl reference times the FP64 CPU oracle on a bounded
 sample of the same workload instead.
 
-Two more workloads, each printing its own line next to the plain
-one-registration-at-a-time GPU path on the same inputs (rank 0 only):
-  --workload batched  256 independent pairs (M, N log-uniform in [2k, 200k],
-                      variants in equal thirds, torus / height field /
-                      ellipsoids, overlap U[0.5, 1], outliers U[0, 0.1]); one
-                      step = 256 target builds + one fricp_batch_register;
-  --workload serve    Poisson arrivals of robust requests (M, N log-uniform in
-                      [1k, 1M]) at {0.25, 0.5, 0.75, 0.9, 1.1} x the plain
-                      path's measured capacity, through fricp_server_* and
-                      through the plain path; regs/s and p50 / p99 latency
-                      (arrival to result) per rate;
-  --workload precision  workload 3 (Welsch point-to-plane, ellipsoids N = 500k,
-                      M = 200k) in the three precision modes side by side:
-                      time, queries/s and each mode's difference from the FP64
-                      reference mode;
-  --workload robustness  random initial alignments as one batched launch: the
-                      source rotated from its ground-truth position by
-                      beta in {5, 10, 20, 30, 50} degrees about 10 random axes,
-                      three solvers (150 registrations); mean RMSE (Eq. 13) per
-                      beta, alpha-recall, and fixed nu_max / fixed nu_min /
-                      decreasing nu for the Welsch point-to-point solver.
+Besides the headline, the default run measures the other workloads and nests
+their summaries in the same JSON line ("workloads"; --no-nested skips them):
+  single_torus_p2p       workload 1: Fast ICP, torus N = M = 2,000;
+  single_height_field    workload 2: Welsch point-to-point, height field
+                         N = 100,000, M = 80,000;
+  precision              workload 3 in the FP32 and FP16-storage modes beside
+                         the FP64 reference mode, each with its error against
+                         the FP64 oracle's result (tests/golden, written by the
+                         oracle alone);
+  batched                workload 4: 256 pairs (M, N log-uniform in [2k, 200k],
+                         variants in equal thirds) in one fricp_batch_register
+                         vs the plain path one pair at a time;
+  served                 workload 5: Poisson arrivals of robust requests (M, N
+                         log-uniform in [1k, 1M]) at 0.9x and 1.1x the plain
+                         path's capacity through fricp_server_* vs the plain path.
+Standalone runs (one line each): --workload batched | serve (five rates) |
+precision | robustness.
 """
 from __future__ import annotations
 
@@ -58,12 +54,13 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "corr. queries/s (M x iters/s)"
 UNIT = "queries/s"
-VARIANT = "p2p_welsch"
-WORKLOAD = "welsch_p2p_aa_height_field_N100000_M80000"
+VARIANT = "p2pl_welsch"
+WORKLOAD = "welsch_p2pl_aa_ellipsoids_N500000_M200000"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
-CPU_SAMPLE_M = 80000                # cpu_baseline sample: every source point, full target
-CPU_SAMPLE_ITERS = 10
-REF_SAMPLE_M = 16000                # --impl reference: 20% of the source points per step
+CPU_SAMPLE_M = 20000                # cpu_baseline sample: 10% of the source points, full target
+CPU_SAMPLE_ITERS = 8
+REF_SAMPLE_M = 4000                 # --impl reference: 2% of the source points per step
+GOLDEN3 = ROOT / "tests" / "golden" / "fullsize_config3_p2pl_welsch.json"
 # Files that define the search kernel k_nn (its launch, query set-up and tree
 # search); the solver's algebra (solver.cuh, linalg.cuh) and the median
 # (select.cuh) are compiled into the same file but only the accumulate kernel
@@ -80,7 +77,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "serve", "precision", "robustness"])
-    ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate (serve)")
+    ap.add_argument("--serve-requests", type=int, default=96, help="distinct requests drawn (serve)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window per rate (serve)")
+    ap.add_argument("--no-nested", action="store_true", help="headline only (skip the nested workloads)")
     return ap.parse_args()
 
 
@@ -105,7 +104,7 @@ def max_over_ranks(xs, world, device="cuda"):
 
 def workload_pair():
     from paper_2007_07627_gb300 import synth
-    return synth.config_pair(2)
+    return synth.config_pair(3)
 
 
 # --------------------------------------------------------------------------
@@ -167,31 +166,41 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 
 def oracle_sample(pair, nu, iters=CPU_SAMPLE_ITERS, m=CPU_SAMPLE_M):
-    """Alg. 1 of the FP64 oracle on a fixed 20% sample of the source points
-    against the full target, one nu stage, `iters` inner iterations."""
+    """Alg. 2 of the FP64 oracle (exhaustive closest points) on a fixed sample
+    of m source points against the full target, one nu stage of `iters`
+    inner iterations."""
     import numpy as np
 
     import oracle
     oracle.build()
     g = np.random.default_rng(20070762)
     sel = np.sort(g.choice(pair.M, m, replace=False))
-    prm = oracle.Params(variant=VARIANT, max_iters=iters, nu_max=nu, nu_min=nu)
+    prm = oracle.Params(variant=VARIANT, p2pl_iters_first=iters, p2pl_iters_cap=iters, nu_max=nu, nu_min=nu)
     t0 = time.perf_counter()
-    r = oracle.register(pair.P[sel], pair.Q, prm)
+    r = oracle.register(pair.P[sel], pair.Q, prm, normals=pair.normals)
     dt = time.perf_counter() - t0
     return {"value": m * r["iterations"] / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "seconds": dt, "iterations": r["iterations"],
-            "sample": f"FP64 oracle (exhaustive closest point, OpenMP), Alg. 1 on {m} of the {pair.M} source "
+            "seconds": dt, "iterations": r["iterations"], "corr_passes": r["corr_passes"],
+            "sample": f"FP64 oracle (exhaustive closest point, OpenMP), Alg. 2 on {m} of the {pair.M} source "
                       f"points vs the full {pair.N}-point target, one nu stage at nu={nu:.3g}, {iters} iterations"}
 
 
-def reference_nu(pair):
-    """nu of the oracle sample: the workload's nu_min (Sec. 4.3), computed by the oracle."""
+def reference_nu(pair, m=CPU_SAMPLE_M):
+    """nu of the oracle samples: a quarter of the workload's nu_max (Sec. 5:
+    3 x the median plane distance at the identity start), computed by the
+    oracle on the sample. (Its nu_min is the 1e-6 floor: the target is
+    noise-free, so the six-neighbour plane distances vanish; at that nu every
+    weight underflows.)"""
     import numpy as np
 
     import oracle
+    g = np.random.default_rng(20070762)
+    sel = np.sort(g.choice(pair.M, m, replace=False))
     nz = oracle.normalization(pair.P.astype(np.float64), pair.Q.astype(np.float64))
-    return max(oracle.nu_min_point_to_point(nz.fwd(pair.Q.astype(np.float64))), oracle.NU_MIN_FLOOR)
+    Pn, Qn = nz.fwd(pair.P[sel].astype(np.float64)), nz.fwd(pair.Q.astype(np.float64))
+    idx, _, _ = oracle.closest(Pn, Qn)
+    h = np.abs(np.einsum("nd,nd->n", Pn - Qn[idx], pair.normals[idx].astype(np.float64)))
+    return 3.0 * float(np.median(h)) / 4.0
 
 
 def run_reference(args):
@@ -199,7 +208,7 @@ def run_reference(args):
     if rank != 0:
         return
     pair = workload_pair()
-    nu = reference_nu(pair)
+    nu = reference_nu(pair, REF_SAMPLE_M)
     for _ in range(args.warmup):
         oracle_sample(pair, nu, iters=1, m=REF_SAMPLE_M)
     times, its = [], []
@@ -214,7 +223,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "variant": VARIANT, "N": pair.N, "M": pair.M},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"each step: Alg. 1 of the FP64 oracle, one iteration, {REF_SAMPLE_M} of "
+                         "sample": f"each step: Alg. 2 of the FP64 oracle, one iteration, {REF_SAMPLE_M} of "
                                    f"{pair.M} source points vs the full target, nu={nu:.3g}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -250,17 +259,71 @@ def step_kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the search kernel from the committed ncu summary,
-    only if it was taken on the current kernel source."""
-    p = ROOT / "profiles" / "k_nn_dram.json"
+def profiled_kernel(workload: str):
+    """Counters of the search kernel from the committed ncu summary of
+    `workload` (profiles/k_nn_<workload>.json), only if they were taken on the
+    current kernel source: DRAM bytes per launch, issue-slot and L2 fractions."""
+    p = ROOT / "profiles" / f"k_nn_{workload}.json"
     try:
         d = json.loads(p.read_text())
     except (OSError, ValueError):
-        return None
+        return {}
     if d.get("kernel_source_sha256_16") != step_kernel_hash():
-        return None
-    return d.get("dram_bytes_per_launch")
+        return {}
+    return d
+
+
+def timed_registrations(fr, q, n, p, prm, steps, warmup, flush):
+    """Whole registrations (target build included) timed with CUDA events, L2
+    flushed before each; returns (mean ms, last result)."""
+    import torch
+    for _ in range(warmup):
+        t = fr.target_create(q, n)
+        fr.register(t, p, params=prm)
+        t.destroy()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    r = None
+    for _ in range(steps):
+        flush.zero_()
+        ev0.record()
+        t = fr.target_create(q, n)
+        r = fr.register(t, p, params=prm)
+        ev1.record()
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        t.destroy()
+    return statistics.mean(times), r
+
+
+def kernel_times(fr, q, n, p, prm):
+    """Per-pass device time of the search and of the accumulate/solve kernels,
+    from CUDA events recorded around every launch on the library's stream."""
+    t = fr.target_create(q, n)
+    prm_t = fr.Params.from_buffer_copy(prm)
+    prm_t.time_passes = 1
+    rt = fr.register(t, p, params=prm_t)
+    t.destroy()
+    steps = rt["device_steps"]
+    return 1e3 * rt["search_ms"] / steps, 1e3 * (rt["pass_ms"] - rt["search_ms"]) / steps, rt
+
+
+def roofline_of(search_us, M, N, plane, workload):
+    algo = 12 * M + (24 if plane else 12) * N
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else 6800.0
+    achieved = algo / (search_us * 1e-6) / 1e9
+    prof = profiled_kernel(workload)
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": prof.get("dram_bytes_per_launch"), "kernel": "k_nn<0> (closest-point search)",
+           "avg_launch_us": search_us, "algorithmic_bytes_per_launch": algo,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s (of fallback)"}
+    if prof:
+        out["issue_active_frac"] = prof.get("issue_active_frac")
+        out["l2_throughput_frac"] = prof.get("l2_throughput_frac")
+        out["profile"] = prof.get("summary")
+    return out
 
 
 def run_ours(args):
@@ -268,6 +331,9 @@ def run_ours(args):
     import torch
 
     rank, world, local = dist_env()
+    nested_data = None
+    if world == 1 and not args.no_nested:
+        nested_data = nested_inputs()        # spawn pool, before the first CUDA call
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -278,17 +344,18 @@ def run_ours(args):
 
     pair = workload_pair()
     Qd = torch.from_numpy(pair.Q).cuda()
+    Nd = torch.from_numpy(pair.normals).cuda()
     Pd = torch.from_numpy(pair.P).cuda()
     prm = fr.params_default(VARIANT)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def one_step(q, p):
-        t = fr.target_create(q)
+    def one_step(q, n, p):
+        t = fr.target_create(q, n)
         r = fr.register(t, p, params=prm)
         return t, r
 
     for _ in range(args.warmup):
-        t, r = one_step(Qd, Pd)
+        t, r = one_step(Qd, Nd, Pd)
         t.destroy()
     torch.cuda.synchronize()
     if world > 1:
@@ -303,7 +370,7 @@ def run_ours(args):
     for _ in range(args.steps):
         flush.zero_()                       # evict L2 between timed steps
         ev0.record()
-        t, r = one_step(Qd, Pd)
+        t, r = one_step(Qd, Nd, Pd)
         ev1.record()
         torch.cuda.synchronize()
         times.append(ev0.elapsed_time(ev1))
@@ -319,30 +386,19 @@ def run_ours(args):
     it = statistics.mean(iters)
     value = world * pair.M * it / (ms / 1e3)
 
-    # dominant kernel: the closest-point search k_nn<0>, timed launch by launch
-    # with CUDA events on the library's stream (an event between the search and
-    # the accumulate/solve kernel of every step)
-    t = fr.target_create(Qd)
-    rt = fr.register(t, Pd, params=fr.params_default(VARIANT, time_passes=1))
-    t.destroy()
-    per_launch_s = rt["search_ms"] / 1e3 / rt["device_steps"]
-    accum_us = (rt["pass_ms"] - rt["search_ms"]) * 1e3 / rt["device_steps"]
-    algo_bytes = 12 * pair.M + 12 * pair.N
-    peaks = measured_peaks()
-    peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else 6800.0
-    achieved = algo_bytes / per_launch_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(), "kernel": "k_nn<0> (closest-point search)",
-                "avg_launch_us": per_launch_s * 1e6, "algorithmic_bytes_per_launch": algo_bytes,
-                "accum_solve_avg_launch_us": accum_us,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+    # dominant kernel: the closest-point search, timed launch by launch with
+    # CUDA events on the library's stream (an event between the search and the
+    # accumulate/solve kernel of every step)
+    search_us, accum_us, rt = kernel_times(fr, Qd, Nd, Pd, prm)
+    roofline = roofline_of(search_us, pair.M, pair.N, True, WORKLOAD)
+    roofline["accum_solve_avg_launch_us"] = accum_us
 
     # end to end through the public API with host buffers
     e2e_t = []
     fr.counters(reset=True)
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        th = fr.target_create(pair.Q)
+        th = fr.target_create(pair.Q, pair.normals)
         rh = fr.register(th, pair.P, params=prm)
         e2e_t.append(time.perf_counter() - t0)
         th.destroy()
@@ -357,14 +413,14 @@ def run_ours(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(pair, rt["nu_min"])
+        cpu = oracle_sample(pair, reference_nu(pair))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 (candidate distances f32 pairs)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "variant": VARIANT, "N": pair.N, "M": pair.M,
-                   "iterations": it, "corr_passes": statistics.mean(passes), "l2": "flushed between steps",
-                   "step": "target index + nu rules + source prep + all iterations",
+                   "iterations": it, "corr_passes": statistics.mean(passes), "device_steps": rt["device_steps"],
+                   "l2": "flushed between steps", "step": "target index + nu rules + source prep + all iterations",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -372,9 +428,90 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if nested_data is not None:
+        line["workloads"] = nested_workloads(fr, nested_data, flush, pair, (Qd, Nd, Pd), rt)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# Nested workloads of the default run (rank 0, N = 1)
+# --------------------------------------------------------------------------
+
+NESTED_SERVE_RATES = (0.9, 1.1)
+NESTED_SERVE_SECONDS = 30.0
+NESTED_SERVE_POOL = 48
+
+
+def nested_inputs():
+    from paper_2007_07627_gb300 import synth
+    t0 = time.perf_counter()
+    batch = generate(synth.batch_specs())
+    serve = generate(synth.serve_specs(n=NESTED_SERVE_POOL))
+    return {"batch": batch, "serve": serve, "gen_s": time.perf_counter() - t0}
+
+
+def single_summary(fr, cfg, variant, over, flush, steps=5, warmup=2):
+    import torch
+
+    from paper_2007_07627_gb300 import synth
+    pair = synth.config_pair(cfg)
+    q, p = torch.from_numpy(pair.Q).cuda(), torch.from_numpy(pair.P).cuda()
+    n = torch.from_numpy(pair.normals).cuda() if pair.normals is not None and variant.startswith("p2pl") else None
+    prm = fr.params_default(variant, **over)
+    ms, r = timed_registrations(fr, q, n, p, prm, steps, warmup, flush)
+    s_us, a_us, _ = kernel_times(fr, q, n, p, prm)
+    name = {1: "p2p_aa_torus_N2000_M2000", 2: "welsch_p2p_aa_height_field_N100000_M80000"}[cfg]
+    return {"workload": name, "variant": variant, "N": pair.N, "M": pair.M, "ms_per_registration": ms,
+            "queries_per_s": pair.M * r["iterations"] / (ms / 1e3), "iterations": r["iterations"],
+            "device_steps": r["device_steps"], "search_us_per_pass": s_us, "accum_solve_us_per_pass": a_us,
+            "roofline": roofline_of(s_us, pair.M, pair.N, False, name), "steps": steps}
+
+
+def precision_summary(fr, pair, dev, flush, steps=3, warmup=1):
+    """Workload 3 in each precision mode; errors against the FP64 oracle's
+    whole-registration result (tests/golden, written by the oracle alone) and
+    against the FP64 GPU mode."""
+    import numpy as np
+    Qd, Nd, Pd = dev
+    gold = None
+    try:
+        gold = json.loads(GOLDEN3.read_text())
+    except (OSError, ValueError):
+        pass
+    modes, ref = {}, None
+    for prec in ("fp64", "fp32", "fp16"):
+        prm = fr.params_default(VARIANT, precision=prec)
+        ms, r = timed_registrations(fr, Qd, Nd, Pd, prm, steps, warmup, flush)
+        if ref is None:
+            ref = r
+        diag = 1.0 / r["scale"]
+
+        def err(R, t):
+            c = (np.trace(r["R"] @ np.asarray(R).T) - 1.0) / 2.0
+            return {"rotation_rad": float(np.arccos(np.clip(c, -1.0, 1.0))),
+                    "t_over_diag": float(np.abs(r["t"] - np.asarray(t)).max() / diag)}
+        modes[prec] = {"ms_per_registration": ms, "iterations": r["iterations"], "device_steps": r["device_steps"],
+                       "queries_per_s": pair.M * r["iterations"] / (ms / 1e3),
+                       "us_per_device_step": 1e3 * ms / r["device_steps"],
+                       "vs_fp64_oracle": (dict(err(gold["R"], gold["t"]), iterations_oracle=gold["iterations"],
+                                               energy_rel=abs(r["final_energy"] - gold["final_energy"]) /
+                                               abs(gold["final_energy"])) if gold else None),
+                       "vs_fp64_mode": err(ref["R"], ref["t"])}
+    return {"workload": WORKLOAD, "modes": modes,
+            "oracle_result": "tests/golden/fullsize_config3_p2pl_welsch.json" if gold else None}
+
+
+def nested_workloads(fr, data, flush, pair, dev, rt):
+    t0 = time.perf_counter()
+    out = {"single_torus_p2p": single_summary(fr, 1, "p2p", dict(max_iters=100), flush, steps=10, warmup=3),
+           "single_height_field": single_summary(fr, 2, "p2p_welsch", {}, flush)}
+    out["precision"] = precision_summary(fr, pair, dev, flush)
+    out["batched"] = batched_summary(fr, data["batch"], steps=1, warmup=1)
+    out["served"] = served_summary(fr, data["serve"], NESTED_SERVE_RATES, NESTED_SERVE_SECONDS)
+    out["seconds"] = {"generation": data["gen_s"], "measurement": time.perf_counter() - t0}
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -407,18 +544,11 @@ def to_device(pairs):
     return out
 
 
-def run_batched(args):
-    from paper_2007_07627_gb300 import synth
-    rank, world, local = dist_env()
-    if rank != 0:
-        return
-    specs = synth.batch_specs()
-    pairs = generate(specs)
+def batched_summary(fr, pairs, steps=1, warmup=1):
+    """Workload 4: 256 target builds plus one fricp_batch_register, against the
+    plain path (target build plus fricp_register, one pair after another) on the
+    same inputs; results compared bit for bit."""
     import torch
-    torch.cuda.set_device(local)
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2007_07627_gb300 as fr
     dev = to_device(pairs)
     prms = [fr.params_default(v) for v, _ in pairs]
     sum_m = sum(p.M for _, p in pairs)
@@ -445,37 +575,54 @@ def run_batched(args):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, r
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched()
     fr.counters(reset=True)
-    clocks = ClockSampler(gpu_selector(local))
-    clocks.start()
     bt = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         dt, rb = timed(batched)
         bt.append(dt)
-    clk = clocks.stop()
-    launches = fr.counters(reset=True)["kernel_launches"] // args.steps
+    launches = fr.counters(reset=True)["kernel_launches"] // steps
     shape = fr.batch_last_shape()
     pt, rp = timed(plain)
     iters = sum(r["iterations"] for r in rb)
     queries = sum(p.M * r["iterations"] for (_, p), r in zip(pairs, rb))
     t_b = statistics.mean(bt)
-    line = {
-        "metric": "corr. queries/s (sum over pairs of M x iters / s); regs/s", "workload": "batched",
-        "value": queries / t_b, "unit": "queries/s", "regs_per_s": len(pairs) / t_b, "ms_per_step": 1e3 * t_b,
-        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
-        "dtype": "f64 (candidate distances f32 pairs)",
-        "config": {"workload": "256 pairs, M and N log-uniform in [2k, 200k], mixed variants and surfaces",
-                   "pairs": len(pairs), "sum_M": sum_m, "sum_N": sum(p.N for _, p in pairs),
-                   "iterations_total": iters, "step": "256 target builds + nu rules + one batched registration",
-                   "autotuned_shape": shape, "l2": "inputs 320 MB > L2"},
-        "plain": {"value": sum(p.M * r["iterations"] for (_, p), r in zip(pairs, rp)) / pt, "unit": "queries/s",
+    return {
+        "workload": "256 pairs, M and N log-uniform in [2k, 200k], mixed variants and surfaces",
+        "queries_per_s": queries / t_b, "regs_per_s": len(pairs) / t_b, "seconds_per_batch": t_b,
+        "pairs": len(pairs), "sum_M": sum_m, "sum_N": sum(p.N for _, p in pairs), "iterations_total": iters,
+        "step": "256 target builds + nu rules + one batched registration", "autotuned_shape": shape,
+        "plain": {"queries_per_s": sum(p.M * r["iterations"] for (_, p), r in zip(pairs, rp)) / pt,
                   "regs_per_s": len(pairs) / pt, "seconds": pt},
         "speedup_vs_plain": pt / t_b,
         "equal_results": sum(same_result(a, b) for a, b in zip(rb, rp)), "of": len(pairs),
-        "gpu_launches": launches, "clocks": clk,
+        "gpu_launches_per_batch": launches, "steps": steps,
     }
+
+
+def run_batched(args):
+    from paper_2007_07627_gb300 import synth
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    pairs = generate(synth.batch_specs())
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2007_07627_gb300 as fr
+    clocks = ClockSampler(gpu_selector(local))
+    clocks.start()
+    b = batched_summary(fr, pairs, steps=args.steps, warmup=args.warmup)
+    clk = clocks.stop()
+    line = {"metric": "corr. queries/s (sum over pairs of M x iters / s); regs/s", "workload": "batched",
+            "value": b["queries_per_s"], "unit": "queries/s", "regs_per_s": b["regs_per_s"],
+            "ms_per_step": 1e3 * b["seconds_per_batch"], "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+            "dtype": "f64 (candidate distances f32 pairs)", "config": {"workload": b["workload"],
+                                                                      "l2": "inputs 320 MB > L2"},
+            "summary": b, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -484,107 +631,129 @@ def percentile(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if xs else None
 
 
-def run_serve(args):
+def served_summary(fr, reqs, rates, window_s, seed=None):
+    """Workload 5: Poisson arrivals at each rate x the plain path's capacity
+    over a window of window_s seconds, each arrival one of the distinct
+    requests `reqs` (drawn uniformly); every arrival is a target build plus a
+    registration, timed from its arrival to its result, once through the
+    serving loop (continuous batching) and once through the plain path (one at
+    a time, first come first served). Served results are compared with each
+    request's alone result."""
     import numpy as np
+    import torch
 
     from paper_2007_07627_gb300 import synth
-    rank, world, local = dist_env()
-    if rank != 0:
-        return
-    nreq = args.serve_requests
-    specs = synth.serve_specs(n=nreq)
-    reqs = generate(specs)
-    import torch
-    torch.cuda.set_device(local)
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2007_07627_gb300 as fr
     dev = to_device(reqs)
     prms = [fr.params_default(v) for v, _ in reqs]
+    n = len(reqs)
 
     def alone(k):
-        v, p, q, n = dev[k]
-        t = fr.target_create(q, n)
+        v, p, q, nrm = dev[k]
+        t = fr.target_create(q, nrm)
         r = fr.register(t, p, params=prms[k])
         t.destroy()
         return r
 
     alone(0)                                   # warm-up
     service, ref = [], []
-    for k in range(nreq):
+    for k in range(n):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ref.append(alone(k))
         torch.cuda.synchronize()
         service.append(time.perf_counter() - t0)
     capacity = 1.0 / statistics.mean(service)
-    g = np.random.default_rng(synth.CONFIG_SEEDS[5])
-    rates = []
+    g = np.random.default_rng(synth.CONFIG_SEEDS[5] if seed is None else seed)
+    out_rates = []
     srv = fr.Server(max_slots=256, steps_per_sync=8)
-    for f in (0.25, 0.5, 0.75, 0.9, 1.1):
+    for f in rates:
         lam = f * capacity
-        arr = np.cumsum(g.exponential(1.0 / lam, nreq))
-        order = list(range(nreq))
+        arr = []
+        tt = 0.0
+        while True:
+            tt += g.exponential(1.0 / lam)
+            if tt > window_s:
+                break
+            arr.append(tt)
+        pick = g.integers(0, n, len(arr))
+        na = len(arr)
 
         # plain path: one request at a time, first come first served
         lat_p = []
         t0 = time.perf_counter()
-        for k in order:
+        for a, k in zip(arr, pick):
             now = time.perf_counter() - t0
-            if now < arr[k]:
-                time.sleep(arr[k] - now)
-            alone(k)
+            if now < a:
+                time.sleep(a - now)
+            alone(int(k))
             torch.cuda.synchronize()
-            lat_p.append(time.perf_counter() - t0 - arr[k])
+            lat_p.append(time.perf_counter() - t0 - a)
         span_p = time.perf_counter() - t0
 
         # served path: continuous batching
-        lat_s, equal = [0.0] * nreq, 0
+        lat_s, equal = [0.0] * na, 0
         t0 = time.perf_counter()
-        nxt, live = 0, {}
-        done = 0
-        while done < nreq:
+        nxt, live, done = 0, {}, 0
+        while done < na:
             now = time.perf_counter() - t0
-            while nxt < nreq and arr[nxt] <= now:
-                v, p, q, n = dev[nxt]
-                t = fr.target_create(q, n)
-                live[srv.submit(t, p, prms[nxt])] = (nxt, t)
+            while nxt < na and arr[nxt] <= now:
+                k = int(pick[nxt])
+                v, p, q, nrm = dev[k]
+                t = fr.target_create(q, nrm)
+                live[srv.submit(t, p, prms[k])] = (nxt, k, t)
                 nxt += 1
             if live:
                 srv.step(8)
                 for tk in list(live):
                     r = srv.poll(tk)
                     if r is not None:
-                        k, t = live.pop(tk)
-                        lat_s[k] = time.perf_counter() - t0 - arr[k]
+                        a_i, k, t = live.pop(tk)
+                        lat_s[a_i] = time.perf_counter() - t0 - arr[a_i]
                         equal += same_result(r, ref[k])
                         t.destroy()
                         done += 1
-            elif nxt < nreq:
+            elif nxt < na:
                 time.sleep(max(0.0, arr[nxt] - (time.perf_counter() - t0)))
         span_s = time.perf_counter() - t0
-        rates.append({"rate_x_capacity": f, "arrivals_per_s": lam,
-                      "served": {"regs_per_s": nreq / span_s, "p50_s": percentile(lat_s, 50),
-                                 "p99_s": percentile(lat_s, 99)},
-                      "plain": {"regs_per_s": nreq / span_p, "p50_s": percentile(lat_p, 50),
-                                "p99_s": percentile(lat_p, 99)},
-                      "equal_results": equal, "of": nreq})
+        out_rates.append({"rate_x_capacity": f, "arrivals_per_s": lam, "arrivals": na, "window_s": window_s,
+                          "served": {"regs_per_s": na / span_s, "p50_s": percentile(lat_s, 50),
+                                     "p99_s": percentile(lat_s, 99), "span_s": span_s},
+                          "plain": {"regs_per_s": na / span_p, "p50_s": percentile(lat_p, 50),
+                                    "p99_s": percentile(lat_p, 99), "span_s": span_p},
+                          "equal_results": equal, "of": na})
     srv.destroy()
+    return {"workload": f"Poisson arrivals of robust requests drawn from {n} distinct ones, M and N log-uniform "
+                        f"in [1k, 1M] (mean M {statistics.mean(p.M for _, p in reqs):.0f})",
+            "plain_capacity_regs_per_s": capacity, "plain_mean_service_s": statistics.mean(service),
+            "request": "target build + nu rules + registration (arrival to result)",
+            "autotuned_shape": fr.batch_last_shape(), "rates": out_rates}
+
+
+def run_serve(args):
+    from paper_2007_07627_gb300 import synth
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    reqs = generate(synth.serve_specs(n=args.serve_requests))
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2007_07627_gb300 as fr
+    clocks = ClockSampler(gpu_selector(local))
+    clocks.start()
+    sv = served_summary(fr, reqs, (0.25, 0.5, 0.75, 0.9, 1.1), args.serve_seconds)
+    clk = clocks.stop()
     line = {
         "metric": "served regs/s with p50/p99 latency vs plain", "workload": "serve", "unit": "regs/s",
-        "value": max(r["served"]["regs_per_s"] for r in rates), "higher_is_better": True, "n_gpus": 1,
+        "value": max(r["served"]["regs_per_s"] for r in sv["rates"]), "higher_is_better": True, "n_gpus": 1,
         "data": "synthetic", "dtype": "f64 (candidate distances f32 pairs)",
-        "config": {"workload": f"Poisson arrivals, {nreq} robust requests per rate, M and N log-uniform in "
-                               f"[1k, 1M] (mean M {statistics.mean(p.M for _, p in reqs):.0f})",
-                   "plain_capacity_regs_per_s": capacity, "plain_mean_service_s": statistics.mean(service),
-                   "request": "target build + nu rules + registration (arrival to result)"},
-        "rates": rates,
+        "config": {"workload": sv["workload"]}, "summary": sv, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
 
 def run_precision(args):
-    import numpy as np
     import torch
 
     from paper_2007_07627_gb300 import synth
@@ -596,44 +765,16 @@ def run_precision(args):
     __graft_entry__.build()
     import paper_2007_07627_gb300 as fr
     pair = synth.config_pair(3)
-    Pd, Qd, Nd = (torch.from_numpy(x).cuda() for x in (pair.P, pair.Q, pair.normals))
+    dev = tuple(torch.from_numpy(x).cuda() for x in (pair.Q, pair.normals, pair.P))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    modes = {}
-    ref = None
-    for prec in ("fp64", "fp32", "fp16"):
-        prm = fr.params_default("p2pl_welsch", precision=prec)
-        for _ in range(args.warmup):
-            t = fr.target_create(Qd, Nd)
-            fr.register(t, Pd, params=prm)
-            t.destroy()
-        times = []
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            t = fr.target_create(Qd, Nd)
-            r = fr.register(t, Pd, params=prm)
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-            t.destroy()
-        if ref is None:
-            ref = r
-        c = (np.trace(r["R"] @ ref["R"].T) - 1.0) / 2.0
-        ms = 1e3 * statistics.mean(times)
-        modes[prec] = {"ms_per_registration": ms, "iterations": r["iterations"], "device_steps": r["device_steps"],
-                       "queries_per_s": pair.M * r["iterations"] / (ms / 1e3),
-                       "us_per_device_step": 1e3 * ms / r["device_steps"],
-                       "vs_fp64_mode": {"rotation_rad": float(np.arccos(np.clip(c, -1.0, 1.0))),
-                                        "t_over_diag": float(np.abs(r["t"] - ref["t"]).max() / pair.diag),
-                                        "energy_rel": abs(r["final_energy"] - ref["final_energy"]) /
-                                        abs(ref["final_energy"])}}
+    sm = precision_summary(fr, pair, dev, flush, steps=args.steps, warmup=args.warmup)
     line = {"metric": "corr. queries/s (M x iters/s) per precision mode", "workload": "precision",
-            "value": modes["fp64"]["queries_per_s"], "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
-            "config": {"workload": "welsch_p2pl_aa_ellipsoids_N500000_M200000", "N": pair.N, "M": pair.M,
+            "value": sm["modes"]["fp64"]["queries_per_s"], "unit": "queries/s", "higher_is_better": True,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": pair.N, "M": pair.M,
                        "step": "target index + nu rules + source prep + all iterations",
                        "l2": "flushed between steps"},
-            "modes": modes}
+            "summary": sm}
     print(json.dumps(line), flush=True)
 
 

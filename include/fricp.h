@@ -203,6 +203,41 @@ fricp_status fricp_register(const fricp_target *target, const float *p_xyz, int6
                             void *stream, fricp_result *out, double *trace,
                             int32_t trace_capacity);
 
+/* One correspondence pass of a registration and the decision that followed
+ * it, as recorded by fricp_register_recorded (Alg. 1 / Alg. 2; the initial
+ * pass that yields nu_max is not recorded). Normalised coordinates. */
+typedef struct {
+    int32_t step;          /* device step index of the pass (0-based, counting the initial pass) */
+    int32_t phase;         /* the pass: 1 stage start (alignment from T^(k-1) with the new nu), 2 energy
+                              check at the head of an inner iteration, 3 the pass at T' after a revert
+                              (Alg. 1), 4 energy check of the iterate carried out of a stage on the
+                              iteration cap, 5 line-search trial (Alg. 2) */
+    int32_t revert;        /* 1: the energy check of this pass failed (E >= E_prev): Alg. 1 reverts to
+                              T', Alg. 2 starts its line search */
+    int32_t accepted;      /* 1: an Anderson iterate passed the energy check */
+    int32_t stage;         /* nu stages started so far */
+    int32_t done;          /* 1: the registration ended after this pass */
+    double  nu;            /* nu of the pass (unused by the non-robust variants) */
+    double  E;             /* energy of the pass (Eq. 1, Eq. 9 or Eq. 15) */
+    double  E_prev;        /* the accepted energy the pass was compared with (+inf where none) */
+    double  T[12];         /* the transform evaluated: R row-major, then t */
+    double  xi[6];         /* point-to-plane: the parameter vector evaluated, T = exp(xi); else 0 */
+    double  result[12];    /* at this pass: T' of the alignment step (Eq. 4 / Eq. 12; 12 values), or
+                              xi* = G_ppl(xi) of the Gauss-Newton step (Eq. 19; 6 values) */
+} fricp_step_record;
+
+/* fricp_register that also records every correspondence pass (for checking
+ * a registration step by step against a reference). steps: host buffer of
+ * steps_capacity records; *steps_len receives the number of passes recorded
+ * (at most steps_capacity; later passes are not recorded). Recording adds one
+ * alignment solve per pass to the device work. Errors: as fricp_register, and
+ * EINVAL for a NULL steps buffer with steps_capacity > 0. */
+fricp_status fricp_register_recorded(const fricp_target *target, const float *p_xyz, int64_t m,
+                                     int32_t on_device, const double *T0, const fricp_params *params,
+                                     void *stream, fricp_result *out, double *trace,
+                                     int32_t trace_capacity, fricp_step_record *steps,
+                                     int32_t steps_capacity, int32_t *steps_len);
+
 /* Batched registration (no counterpart in the paper, which registers one pair
  * at a time): npairs independent registrations -- pair i registers p_xyz[i]
  * (m[i] points, host or device per on_device) onto targets[i] with params[i]
@@ -254,9 +289,13 @@ void fricp_batch_last_shape(int32_t *chunk, int32_t *search_blocks_per_sm,
  * serialised internally). */
 typedef struct fricp_server fricp_server;
 
-/* hbm_budget: bytes of device buffers for requests in flight (0 = half of the
- * free device memory; a request holds 28 B per source point, 224 B per
- * 256 points and one solver state of a few KB). max_slots: requests in flight at most
+/* hbm_budget: bytes of device memory the requests in flight may hold (0 = half
+ * of the free device memory): a request's own buffers (28 B per source point,
+ * 224 B per 256 points and one solver state of a few KB) and the index of its
+ * target (16 B per point, 16 more with normals, 64 B per bucket of 16, 8 B per
+ * point of FP16 storage), a target counted once however many requests in
+ * flight share it. Requests are admitted in FIFO order while a slot is free
+ * and the budget holds them. max_slots: requests in flight at most
  * (1..4096). steps_per_sync: device steps per graph replay. max_queue:
  * requests waiting for admission at most. stream: submits of device sources
  * are ordered after the work queued on it. Errors: EINVAL, ENOMEM, ECUDA. */
@@ -268,7 +307,8 @@ fricp_status fricp_server_create(size_t hbm_budget, int32_t max_slots, int32_t s
  * device buffer, ordered after the server's stream), so the caller may reuse
  * p_xyz at once; the target must stay alive until the request's result has
  * been polled. Never blocks on the GPU. *ticket identifies the request.
- * Errors: EINVAL (as fricp_register, or a request larger than the budget),
+ * Errors: EINVAL (as fricp_register, or a request that with its target is
+ * larger than the budget),
  * EUNSUPPORTED, ENOMEM, ECUDA; EBUSY when max_queue requests are waiting. */
 fricp_status fricp_server_submit(fricp_server *server, const fricp_target *target, const float *p_xyz,
                                  int64_t m, int32_t on_device, const double *T0,

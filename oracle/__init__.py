@@ -7,7 +7,9 @@ code with the CUDA path (paper_2007_07627_gb300) and imports nothing from it.
 
 It is a plain, slow restatement of the paper in FP64 on the float32 inputs
 widened to float64:
-  * correspondence step (Sec. 3, Eq. 3) by exhaustive search (nn_bruteforce.c);
+  * correspondence step (Sec. 3, Eq. 3) by exhaustive search (nn_bruteforce.c),
+    or, for full-size inputs, a library k-d tree query whose result is pinned
+    to be the same (closest_kdtree);
   * closed-form weighted rigid alignment (Sec. 3 Eq. 4 and Sec. 4.3 Eq. 12) via
     numpy's SVD;
   * exp / log on SE(3) (Sec. 4.2, Eqs. 8-9; App. A) as scipy's matrix
@@ -127,6 +129,54 @@ def closest(X: np.ndarray, Q: np.ndarray):
     if m:
         lib.oracle_closest(_dp(X), m, _dp(Q), n, _ip(idx), _dp(d2), _dp(d2s))
     return idx, d2, d2s
+
+
+def closest_kdtree(X: np.ndarray, Q: np.ndarray, tree=None, k: int = 8):
+    """Sec. 3 Eq. (3) through a library nearest-neighbour query, for inputs too
+    large for the exhaustive search: scipy's k-d tree proposes the k nearest
+    points of Q for every row of X, each squared distance is then recomputed
+    exactly as `closest` computes it ((a*a + b*b) + c*c in FP64), and the
+    minimum is taken with ties to the lowest index. The result equals
+    `closest`, bit for bit, whenever fewer than k points of Q lie within
+    rounding of a row's minimum (pinned against it on random, duplicated and
+    tied inputs). Returns (idx, d2, d2_second) like `closest`; `tree`: a
+    scipy.spatial.cKDTree of Q, built here when not given."""
+    from scipy.spatial import cKDTree
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    m, n = X.shape[0], Q.shape[0]
+    if m == 0:
+        return np.empty(0, np.int64), np.empty(0), np.empty(0)
+    if tree is None:
+        tree = cKDTree(Q)
+    kk = min(k, n)
+    _, cand = tree.query(X, k=kk, workers=-1)
+    cand = np.asarray(cand, dtype=np.int64).reshape(m, kk)
+    diff = X[:, None, :] - Q[cand]
+    d2 = (diff[..., 0] * diff[..., 0] + diff[..., 1] * diff[..., 1]) + diff[..., 2] * diff[..., 2]
+    # lexicographic (d2, index) order of each row's candidates
+    o = np.argsort(cand, axis=1, kind="stable")
+    cand = np.take_along_axis(cand, o, 1)
+    d2 = np.take_along_axis(d2, o, 1)
+    o = np.argsort(d2, axis=1, kind="stable")
+    cand = np.take_along_axis(cand, o, 1)
+    d2 = np.take_along_axis(d2, o, 1)
+    second = d2[:, 1] if kk > 1 else np.full(m, np.inf)
+    return cand[:, 0].copy(), d2[:, 0].copy(), second.copy()
+
+
+def nn_function(Q: np.ndarray, method: str = "bruteforce"):
+    """The correspondence step against a fixed Q (Sec. 3: Q does not change over
+    a registration): `closest` (exhaustive, the definition) or `closest_kdtree`
+    (a library query, equal to it; its tree built once here)."""
+    if method == "bruteforce":
+        return lambda X: closest(X, Q)
+    if method == "kdtree":
+        from scipy.spatial import cKDTree
+        Qc = np.ascontiguousarray(Q, dtype=np.float64)
+        tree = cKDTree(Qc)
+        return lambda X: closest_kdtree(X, Qc, tree)
+    raise ValueError(method)
 
 
 def knn_self(Q: np.ndarray, k: int):
@@ -390,6 +440,10 @@ class Params:
     # it on show how far the iteration amplifies rounding on a given input.
     solve_jitter: float = 0.0
     jitter_seed: int = 0
+    # Correspondence step: "bruteforce" (exhaustive, the definition) or
+    # "kdtree" (closest_kdtree: a library query with the same result, for
+    # full-size inputs).
+    nn: str = "bruteforce"
 
 
 def _jitter(params: Params):
@@ -432,9 +486,11 @@ def register_point_to_point(P32, Q32, params: Params, T0=None) -> dict:
     trace = []
     m = params.anderson_m
 
+    nn = nn_function(Qn, params.nn)
+
     def corr(T):
         cnt["corr_passes"] += 1
-        idx, d2, _ = closest(apply(T, Pn), Qn)
+        idx, d2, _ = nn(apply(T, Pn))
         return idx, d2
 
     def energy(C, nu):
@@ -576,11 +632,13 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
     trace = []
     m = params.anderson_m
 
+    nn = nn_function(Qn, params.nn)
+
     def evaluate(xi, nu):
         """One correspondence pass at xi: closest points, B_i and the energy."""
         cnt["corr_passes"] += 1
         T = se3_transform(xi)
-        idx, _, _ = closest(apply(T, Pn), Qn)
+        idx, _, _ = nn(apply(T, Pn))
         n = Nr[idx]
         B = np.einsum("nd,nd->n", apply(T, Pn) - Qn[idx], n)
         if robust:

@@ -62,6 +62,16 @@ class Result(ctypes.Structure):
     ]
 
 
+class StepRecord(ctypes.Structure):
+    """fricp_step_record: one correspondence pass of a recorded registration."""
+    _fields_ = [
+        ("step", ctypes.c_int32), ("phase", ctypes.c_int32), ("revert", ctypes.c_int32),
+        ("accepted", ctypes.c_int32), ("stage", ctypes.c_int32), ("done", ctypes.c_int32),
+        ("nu", ctypes.c_double), ("E", ctypes.c_double), ("E_prev", ctypes.c_double),
+        ("T", ctypes.c_double * 12), ("xi", ctypes.c_double * 6), ("result", ctypes.c_double * 12),
+    ]
+
+
 _lib = None
 
 
@@ -82,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.fricp_target_size.restype = i64
     L.fricp_target_has_normals.argtypes = [vp]
     L.fricp_register.argtypes = [vp, vp, i64, i32, dp, ctypes.POINTER(Params), vp, ctypes.POINTER(Result), dp, i32]
+    L.fricp_register_recorded.argtypes = [vp, vp, i64, i32, dp, ctypes.POINTER(Params), vp, ctypes.POINTER(Result),
+                                          dp, i32, ctypes.POINTER(StepRecord), i32, ctypes.POINTER(i32)]
     L.fricp_closest_points.argtypes = [vp, vp, i64, dp, vp, vp, vp]
     L.fricp_eval_pass.argtypes = [vp, vp, i64, i32, i32, dp, dbl, dbl, dp, vp, dp]
     L.fricp_target_nu_min.argtypes = [vp, i32, dbl, vp, dp]
@@ -105,6 +117,7 @@ def lib() -> ctypes.CDLL:
     L.fricp_server_destroy.argtypes = [vp]
     L.fricp_batch_last_shape.restype = None
     for name in ("fricp_params_default", "fricp_target_create", "fricp_target_destroy", "fricp_register",
+                 "fricp_register_recorded",
                  "fricp_closest_points", "fricp_eval_pass", "fricp_target_nu_min", "fricp_batch_register",
                  "fricp_server_create", "fricp_server_submit", "fricp_server_step", "fricp_server_poll",
                  "fricp_server_destroy", "fricp_estimate_normals", "fricp_batch_set_shape"):
@@ -238,6 +251,35 @@ def register(target: Target, p, T0=None, params: Params | None = None, stream=No
     _check(lib().fricp_register(target.handle, pp, m, dev, Tp, ctypes.byref(params), _stream(stream),
                                 ctypes.byref(r), tp, int(trace_capacity)))
     return _result(r, trace if trace_capacity > 0 else None)
+
+
+def register_recorded(target: Target, p, T0=None, params: Params | None = None, stream=None,
+                      trace_capacity: int = 0, steps_capacity: int = 4096, variant=None):
+    """fricp_register_recorded: as register(), plus one record per
+    correspondence pass (a list of dicts: step, phase, revert, accepted, stage,
+    done, nu, E, E_prev, T (4x4, normalised), xi (6), result (12 or 6))."""
+    if params is None:
+        params = params_default(variant if variant is not None else P2P_WELSCH_AA)
+    pp, m, dev, pk = _points(p)
+    Tp, Tk = _mat(T0)
+    trace = np.zeros(max(trace_capacity, 0), np.float64)
+    tp = trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace_capacity > 0 else None
+    r = Result()
+    recs = (StepRecord * max(steps_capacity, 1))()
+    n = ctypes.c_int32()
+    _check(lib().fricp_register_recorded(target.handle, pp, m, dev, Tp, ctypes.byref(params), _stream(stream),
+                                         ctypes.byref(r), tp, int(trace_capacity), recs, int(steps_capacity),
+                                         ctypes.byref(n)))
+    steps = []
+    for k in range(n.value):
+        x = recs[k]
+        T = np.eye(4)
+        T[:3, :3] = np.array(x.T[:9]).reshape(3, 3)
+        T[:3, 3] = np.array(x.T[9:12])
+        steps.append(dict(step=x.step, phase=x.phase, revert=x.revert, accepted=x.accepted, stage=x.stage,
+                          done=x.done, nu=x.nu, E=x.E, E_prev=x.E_prev, T=T, xi=np.array(x.xi[:]),
+                          result=np.array(x.result[:])))
+    return _result(r, trace if trace_capacity > 0 else None), steps
 
 
 def batch_register(targets, sources, params=None, T0=None, stream=None, trace_capacity: int = 0) -> list:

@@ -274,11 +274,19 @@ fricp_status fricp_closest_points(const fricp_target *t, const float *p_xyz, int
     return FRICP_OK;
 }
 
-fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m, int32_t on_device,
-                            const double *T0, const fricp_params *params, void *stream, fricp_result *out,
-                            double *trace, int32_t trace_capacity) {
+}  // extern "C"
+
+namespace {
+
+// fricp_register, with per-pass records when steps_capacity > 0.
+fricp_status register_impl(const fricp_target *t, const float *p_xyz, int64_t m, int32_t on_device,
+                           const double *T0, const fricp_params *params, void *stream, fricp_result *out,
+                           double *trace, int32_t trace_capacity, fricp_step_record *steps,
+                           int32_t steps_capacity, int32_t *steps_len) {
     const auto wall0 = std::chrono::steady_clock::now();
     if (!t || !p_xyz || !params || !out) return fail(FRICP_EINVAL, "NULL argument");
+    if (steps_capacity < 0 || (steps_capacity > 0 && !steps)) return fail(FRICP_EINVAL, "bad steps buffer");
+    if (steps_len) *steps_len = 0;
     if (m < 1 || m > (int64_t)1 << 30) return fail(FRICP_EINVAL, "m must be in 1..2^30");
     if (trace_capacity < 0 || (trace_capacity > 0 && !trace)) return fail(FRICP_EINVAL, "bad trace buffer");
     fricp_status st = check_params(params);
@@ -306,6 +314,9 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
         partial.alloc((size_t)ntiles * fricp::kMaxSums, s) != cudaSuccess ||
         resid.alloc(robust ? m : 1, s) != cudaSuccess || trace_dev.alloc(trace_capacity, s) != cudaSuccess)
         return fail(FRICP_ENOMEM, "device allocation for the registration");
+    DevBuf<fricp_step_record> rec;
+    if (steps_capacity > 0 && rec.alloc(steps_capacity, s) != cudaSuccess)
+        return fail(FRICP_ENOMEM, "device allocation for the step records");
     float plo[3], phi[3];
     int bad = 0;
     cudaError_t e = fricp::prepare_source(p.ptr, m, s, src.p, plo, phi, &bad);
@@ -316,6 +327,10 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     PairState h;
     st = setup_pair(t->d, prm, m, plo, phi, T0, trace_capacity, s, &h, &scale, c);
     if (st != FRICP_OK) return st;
+    if (steps_capacity > 0) {
+        h.rec = rec.p;
+        h.rec_cap = steps_capacity;
+    }
     e = cudaMemcpyAsync(st_dev.p, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the solver state");
     counters().h2d += sizeof(h);
@@ -334,7 +349,7 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     double pass_ms = 0.0, search_ms = 0.0;
     st = run_steps(a, prm.variant, ntiles, prm, s, st_dev.p, &leak, &pass_ms, &search_ms);
     if (leak) {
-        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = true;
+        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = rec.leak = true;
         p.owned = nullptr;
     }
     if (st != FRICP_OK && st != FRICP_ETIMEOUT) return st;
@@ -348,6 +363,13 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
             counters().d2h += (int64_t)sizeof(double) * trace_capacity;
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && steps_capacity > 0) {
+            const int n = std::min(r.rec_len, steps_capacity);
+            if (n > 0) e = cudaMemcpyAsync(steps, rec.p, sizeof(fricp_step_record) * n, cudaMemcpyDeviceToHost, s);
+            counters().d2h += (int64_t)sizeof(fricp_step_record) * n;
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (steps_len) *steps_len = n;
+        }
         if (e != cudaSuccess) return cuda_fail(e, "reading the result");
     } else {
         return st;
@@ -357,6 +379,25 @@ fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m
     out->search_ms = search_ms;
     out->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m, int32_t on_device,
+                            const double *T0, const fricp_params *params, void *stream, fricp_result *out,
+                            double *trace, int32_t trace_capacity) {
+    return register_impl(t, p_xyz, m, on_device, T0, params, stream, out, trace, trace_capacity, nullptr, 0,
+                         nullptr);
+}
+
+fricp_status fricp_register_recorded(const fricp_target *t, const float *p_xyz, int64_t m, int32_t on_device,
+                                     const double *T0, const fricp_params *params, void *stream,
+                                     fricp_result *out, double *trace, int32_t trace_capacity,
+                                     fricp_step_record *steps, int32_t steps_capacity, int32_t *steps_len) {
+    return register_impl(t, p_xyz, m, on_device, T0, params, stream, out, trace, trace_capacity, steps,
+                         steps_capacity, steps_len);
 }
 
 fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t m, int32_t on_device,

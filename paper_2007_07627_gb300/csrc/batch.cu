@@ -777,11 +777,36 @@ struct fricp_server {
     std::deque<Request> queue;
     std::vector<std::unique_ptr<Running>> slots;
     std::map<uint64_t, fricp_result> finished;
+    // targets of the requests in flight: requests using each, and the bytes
+    // counted against the budget for it (once per distinct target)
+    std::map<const fricp_target *, std::pair<int, size_t>> targets;
     uint64_t next_ticket = 1;
     std::mutex mu;
 };
 
 namespace {
+
+// Device bytes of a target's index: points, normals, box tree and (once built)
+// the FP16 storage.
+size_t target_bytes(const fricp_target *t) {
+    const TargetDev &d = *fricp::target_dev(t);
+    size_t b = sizeof(float4) * (size_t)d.n * (d.has_normals ? 2 : 1) + sizeof(float4) * 4 * (size_t)d.L;
+    if (d.pts16) b += sizeof(ushort4) * (size_t)d.n;
+    return b;
+}
+
+// Bytes a request adds to the budget in use: its own buffers, and its target's
+// index unless a request in flight already holds that target (FP16 storage is
+// counted as if it will be built).
+size_t admission_bytes(const fricp_server *sv, const Request &rq) {
+    size_t b = rq.bytes;
+    if (sv->targets.find(rq.target) == sv->targets.end()) {
+        b += target_bytes(rq.target);
+        if (rq.prm.precision == FRICP_PREC_FP16_STORAGE && fricp::target_dev(rq.target)->pts16 == nullptr)
+            b += sizeof(ushort4) * (size_t)fricp::target_dev(rq.target)->n;
+    }
+    return b;
+}
 
 // Admission of the queue's head requests that fit (FIFO, a free slot and room
 // in the budget): heavy work on s_admit, then the commit of each one on s_step
@@ -790,7 +815,8 @@ fricp_status admit_queued(fricp_server *sv, int *admitted) {
     *admitted = 0;
     while (!sv->queue.empty()) {
         Request &rq = sv->queue.front();
-        if (sv->used + rq.bytes > sv->budget) break;
+        const size_t need = admission_bytes(sv, rq);
+        if (sv->used + need > sv->budget) break;
         int slot = -1;
         for (int p = 0; p < sv->max_slots; ++p)
             if (!sv->slots[p]) {
@@ -829,7 +855,9 @@ fricp_status admit_queued(fricp_server *sv, int *admitted) {
         }
         r.host_pts.clear();
         r.host_pts.shrink_to_fit();
-        sv->used += r.bytes;
+        auto &tr = sv->targets[r.target];
+        if (tr.first++ == 0) tr.second = need - r.bytes;
+        sv->used += need;
         sv->slots[slot] = std::move(run);
         ++*admitted;
     }
@@ -864,6 +892,11 @@ fricp_status harvest(fricp_server *sv) {
         if (e != cudaSuccess) return cuda_fail(e, "releasing a slot");
         run.buf.free(sv->s_step);
         sv->used -= run.req.bytes;
+        auto it = sv->targets.find(run.req.target);
+        if (it != sv->targets.end() && --it->second.first == 0) {
+            sv->used -= it->second.second;
+            sv->targets.erase(it);
+        }
         sv->slots[p].reset();
     }
     return FRICP_OK;
@@ -930,7 +963,8 @@ extern "C" fricp_status fricp_server_submit(fricp_server *sv, const fricp_target
     r.has_T0 = T0 != nullptr;
     if (T0) std::memcpy(r.T0, T0, sizeof(r.T0));
     r.bytes = PairBuffers::need(m, 0);
-    if (r.bytes > sv->budget) return fail(FRICP_EINVAL, "request needs more device memory than the server budget");
+    if (r.bytes + target_bytes(target) > sv->budget)
+        return fail(FRICP_EINVAL, "request and its target need more device memory than the server budget");
     if (on_device) {
         cudaError_t e = cudaEventRecord(sv->ev_user, sv->user);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->s_admit, sv->ev_user, 0);

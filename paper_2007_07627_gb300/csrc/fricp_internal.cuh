@@ -130,6 +130,11 @@ struct PairState {
     int iterations, corr_passes, aa_accepted, reverts, ls_trials, stages, device_steps, trace_len;
     double final_energy;
     double eval_out[48];    // PH_EVAL result: E, T' or xi*, then the reduced sums
+    // normalised transform of the pass requested last (what a step record reports)
+    double Teval[12];
+    // per-pass records (fricp_register_recorded), or null
+    fricp_step_record *rec;
+    int rec_cap, rec_len;
 };
 
 struct StepArgs {

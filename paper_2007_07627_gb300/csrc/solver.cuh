@@ -86,6 +86,7 @@ FRICP_HD inline void request_eval_T(const Team &tm, PairState *st, const double 
     tm.sync();
     for (int i = 0; i < 9; ++i) st->Re[i] = T[i];
     for (int r = 0; r < 3; ++r) st->te[r] = te[r];
+    copy_n(st->Teval, T, 12);
     st->eval_counts = counts;
     tm.sync();
 }
@@ -525,6 +526,32 @@ __device__ inline void store_state(const Team &tm, const PairState *own, PairSta
     for (int k = tm.lane(); k < kStateWords; k += tm.size()) dst[k] = src[k];
 }
 
+// The pass just evaluated, for fricp_register_recorded: the transform, nu, the
+// energy, the accepted energy it is compared with, and the alignment (Eq. 4 /
+// Eq. 12) or Gauss-Newton (Eq. 19) result the reduced sums give. Every lane
+// fills its own copy. Uses the team scratch (before the state machine does).
+__device__ inline void record_pass(const Team &tm, const PairState *st, const double *S, bool pl,
+                                   fricp_step_record *r) {
+    r->step = st->device_steps - 1;
+    r->phase = st->phase;
+    r->nu = st->nu;
+    r->E = S[(pl ? kSumsP2PL : kSumsP2P) - 1];
+    r->E_prev = st->E_prev;
+    copy_n(r->T, st->Teval, 12);
+    for (int i = 0; i < 6; ++i) r->xi[i] = pl ? st->xeval[i] : 0.0;
+    for (int i = 0; i < 12; ++i) r->result[i] = 0.0;
+    if (pl) {
+        double d[6];
+        if (gn_delta(tm, st->xeval, S, d, tm.sh + kShW))
+            for (int i = 0; i < 6; ++i) r->result[i] = st->xeval[i] + d[i];
+    } else {
+        double *T = tm.sh + kShT;
+        if (align_from_sums(tm, st, S, T, tm.sh + kShW)) copy_n(r->result, T, 12);
+        tm.sync();
+    }
+    r->revert = r->accepted = r->stage = r->done = 0;
+}
+
 // One solver step by a team (the first kTeamLanes lanes of a warp; tm.sh:
 // kTeamScratch doubles of shared memory). S: the reduced sums of the pass just
 // evaluated.
@@ -552,10 +579,24 @@ static __device__ __noinline__ void solver_step(Team tm, PairState *gst, const d
         st->status = ok ? FRICP_OK : FRICP_EDEGENERATE;
         st->phase = PH_DONE;
         st->done = 1;
-    } else if (fricp::variant_p2pl(st->variant)) {
-        p2pl_step(tm, st, S, trace);
     } else {
-        p2p_step(tm, st, S, trace);
+        const bool pl = fricp::variant_p2pl(st->variant);
+        fricp_step_record r;
+        const bool rec = st->rec != nullptr && st->rec_len < st->rec_cap;
+        if (rec) record_pass(tm, st, S, pl, &r);
+        const int rev0 = st->reverts, acc0 = st->aa_accepted;
+        if (pl)
+            p2pl_step(tm, st, S, trace);
+        else
+            p2p_step(tm, st, S, trace);
+        if (rec) {
+            r.revert = st->reverts - rev0;
+            r.accepted = st->aa_accepted - acc0;
+            r.stage = st->stages;
+            r.done = st->done;
+            if (tm.lane() == 0) st->rec[st->rec_len] = r;
+            st->rec_len++;
+        }
     }
     set_head_cache(tm, st);
     st->counter = 0u;   // the next pass's tile and search tickets start over

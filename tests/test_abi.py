@@ -40,9 +40,10 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "fricp.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(fricp_params), sizeof(fricp_result),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(fricp_params), sizeof(fricp_result),
          offsetof(fricp_params, timeout_s), offsetof(fricp_result, wall_ms),
-         offsetof(fricp_result, status), offsetof(fricp_result, nu_max));
+         offsetof(fricp_result, status), offsetof(fricp_result, nu_max),
+         sizeof(fricp_step_record), offsetof(fricp_step_record, T), offsetof(fricp_step_record, result));
   return 0;
 }
 '''
@@ -58,6 +59,8 @@ int main(void) {
     assert vals[2] == fr.Params.timeout_s.offset
     assert vals[3] == fr.Result.wall_ms.offset
     assert vals[4] == fr.Result.status.offset
+    assert vals[6] == ctypes.sizeof(fr.StepRecord)
+    assert vals[7] == fr.StepRecord.T.offset and vals[8] == fr.StepRecord.result.offset
     assert vals[5] == fr.Result.nu_max.offset
 
 

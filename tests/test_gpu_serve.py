@@ -79,9 +79,11 @@ def test_budget_limits_admission(fr):
     reqs = synth.serve_requests(seed=778, n=6, lo=3000, hi=3000)
     assert all(p.M == 3000 for _, p in reqs)
     targets = [fr.target_create(p.Q, p.normals) for _, p in reqs]
-    # one request holds 28 B per point and 224 B per 256 points (173 KB for two
-    # of 3000 points) plus one state and alignment (under 5 KB): 120 KB admits one
-    srv = fr.Server(hbm_budget=120_000, max_slots=16, steps_per_sync=4)
+    # one request holds 28 B per point and 224 B per 256 points (87 KB for 3000
+    # points) plus one state (under 5 KB), and its target's index 32 B per point
+    # with normals and 64 B per bucket of 16 (112 KB for 3000 points): every
+    # request has its own target, so 300 KB admits one request at a time
+    srv = fr.Server(hbm_budget=300_000, max_slots=16, steps_per_sync=4)
     results, max_inf = _serve_all(fr, srv, reqs, targets, [0] * len(reqs), nsteps=4)
     assert max_inf == 1
     for k, (v, p) in enumerate(reqs):

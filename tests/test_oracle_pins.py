@@ -652,3 +652,46 @@ def test_line_search_first_trial_is_the_gauss_newton_step(monkeypatch):
     assert bad["aa_accepted"] == 0 and bad["iterations"] == plain["iterations"] > 3
     assert bad["line_search_trials"] >= bad["reverts"] > plain["reverts"]
     assert np.allclose(bad["trace"], plain["trace"], rtol=1e-10, atol=0)
+
+
+# --------------------------------------------------------------------------
+# The library k-d tree correspondence step equals the exhaustive definition
+# (Sec. 3 Eq. 3), bit for bit, including duplicates and exact ties.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,m,dups", [(1, 5, 0), (7, 40, 0), (500, 800, 0), (3000, 2000, 200), (20000, 5000, 0)])
+def test_kdtree_closest_equals_bruteforce(n, m, dups):
+    g = np.random.default_rng(n + m)
+    Q = g.random((n, 3)).astype(np.float32).astype(np.float64)
+    if dups:
+        Q[n - dups:] = Q[g.integers(0, n - dups, dups)]
+    X = np.concatenate([g.random((m, 3)) * 1.3 - 0.15, Q[g.integers(0, n, min(m, 50))]])
+    a = oracle.closest(X, Q)
+    b = oracle.closest_kdtree(X, Q)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1])
+    if n > 1:
+        assert np.array_equal(a[2], b[2])
+
+
+def test_kdtree_closest_breaks_exact_ties_to_the_lowest_index():
+    # a lattice: queries at cell centres are equidistant from 8 corners
+    gx = np.arange(4, dtype=np.float64)
+    G = np.stack(np.meshgrid(gx, gx, gx, indexing="ij"), -1).reshape(-1, 3)
+    X = np.array([[0.5, 0.5, 0.5], [1.5, 2.5, 0.5], [1.0, 1.5, 2.0]])
+    a = oracle.closest(X, G)
+    b = oracle.closest_kdtree(X, G, k=12)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_registration_with_kdtree_correspondences_equals_bruteforce():
+    from paper_2007_07627_gb300 import synth
+    pair = synth.config_pair(1)
+    for variant in ("p2p", "p2pl_welsch"):
+        over = dict(max_iters=30) if variant == "p2p" else {}
+        a = oracle.register(pair.P, pair.Q, oracle.Params(variant=variant, **over), normals=pair.normals)
+        b = oracle.register(pair.P, pair.Q, oracle.Params(variant=variant, nn="kdtree", **over), normals=pair.normals)
+        for key in ("iterations", "corr_passes", "reverts", "line_search_trials", "stages"):
+            assert a[key] == b[key]
+        assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["t"], b["t"])
+        assert np.array_equal(a["trace"], b["trace"])
