@@ -31,7 +31,7 @@ their summaries in the same JSON line ("workloads"; --no-nested skips them):
                          variants in equal thirds) in one fricp_batch_register
                          vs the plain path one pair at a time;
   served                 workload 5: Poisson arrivals of robust requests (M, N
-                         log-uniform in [1k, 1M]) at 0.9x and 1.1x the plain
+                         log-uniform in [1k, 1M]) at 0.9x, 1.1x and 1.5x the plain
                          path's capacity through fricp_server_* vs the plain path.
 Standalone runs (one line each): --workload batched | serve (five rates) |
 precision | robustness.
@@ -439,8 +439,8 @@ def run_ours(args):
 # Nested workloads of the default run (rank 0, N = 1)
 # --------------------------------------------------------------------------
 
-NESTED_SERVE_RATES = (0.9, 1.1)
-NESTED_SERVE_SECONDS = 30.0
+NESTED_SERVE_RATES = (0.9, 1.1, 1.5)
+NESTED_SERVE_SECONDS = 25.0
 NESTED_SERVE_POOL = 48
 
 
@@ -742,7 +742,7 @@ def run_serve(args):
     import paper_2007_07627_gb300 as fr
     clocks = ClockSampler(gpu_selector(local))
     clocks.start()
-    sv = served_summary(fr, reqs, (0.25, 0.5, 0.75, 0.9, 1.1), args.serve_seconds)
+    sv = served_summary(fr, reqs, (0.25, 0.5, 0.75, 0.9, 1.1, 1.5), args.serve_seconds)
     clk = clocks.stop()
     line = {
         "metric": "served regs/s with p50/p99 latency vs plain", "workload": "serve", "unit": "regs/s",

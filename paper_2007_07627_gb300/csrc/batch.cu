@@ -330,6 +330,7 @@ class BatchEngine {
     BatchShape shape{1, 0, 0};
     host::Graph graph;
     int graph_steps = 0;
+    BatchShape graph_shape{0, 0, 0, 0};   // the shape the graph was captured with
     int64_t graph_kernels = 0;   // kernel nodes per replay
     cudaStream_t s = nullptr;
 
@@ -395,7 +396,10 @@ class BatchEngine {
     // Graph of `steps` device steps followed by a plan (so that ctl and the done
     // flags describe the state after the last step).
     cudaError_t capture(int steps) {
-        if (graph.exec && graph_steps == steps) return cudaSuccess;
+        if (graph.exec && graph_steps == steps && graph_shape.chunk == shape.chunk &&
+            graph_shape.nn_per_sm == shape.nn_per_sm && graph_shape.acc_per_sm == shape.acc_per_sm &&
+            graph_shape.order == shape.order)
+            return cudaSuccess;
         graph.reset();
         const int64_t before = counters().launches;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -407,6 +411,7 @@ class BatchEngine {
         if (e == cudaSuccess) e = cudaGraphInstantiate(&graph.exec, graph.g, 0);
         if (e == cudaSuccess) {
             graph_steps = steps;
+            graph_shape = shape;
             graph_kernels = host::graph_kernel_nodes(graph.g);
         }
         return e;
@@ -457,9 +462,11 @@ class BatchEngine {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        // (chunk, order): tickets from the counter, fixed strides, query tiles
-        const int cands[][2] = {{1, kOrderCounter}, {2, kOrderCounter}, {4, kOrderCounter}, {8, kOrderCounter},
-                                {16, kOrderCounter}, {1, kOrderStride}, {2, kOrderStride}, {kTileQ, kOrderTiles}};
+        // (chunk, order): query tiles, tickets of 1 or 4 queries from the counter,
+        // single queries in a fixed stride (the shapes that have won on some
+        // size class: tiles on every mix of many or large registrations, the
+        // others on a few small ones)
+        const int cands[][2] = {{kTileQ, kOrderTiles}, {4, kOrderCounter}, {1, kOrderCounter}, {1, kOrderStride}};
         int per_sm[2] = {nn_max, (nn_max + 1) / 2};
         BatchShape best{1, nn_max, acc_max, 0};
         float best_ms = 1e30f;
@@ -773,6 +780,7 @@ struct fricp_server {
     int steps_per_graph = 16;
     int max_queue = 0;
     bool tuned = false;
+    std::pair<int, int> tuned_class{-1, -1};   // size class the step graph's shape was tuned for
     double timeout_s = 600.0;
     std::deque<Request> queue;
     std::vector<std::unique_ptr<Running>> slots;
@@ -993,14 +1001,24 @@ extern "C" fricp_status fricp_server_step(fricp_server *sv, int32_t nsteps, int3
     if (!sv->tuned) {
         st = admit_queued(sv, &admitted);
         if (st != FRICP_OK) return st;
-        if (admitted > 0) {
-            int64_t pts = 0;
-            for (const auto &r : sv->slots)
-                if (r) pts += r->req.m;
-            cudaError_t e = sv->eng.tune(pts, count_in_flight(sv));
-            if (e == cudaSuccess) e = sv->eng.capture(sv->steps_per_graph);
-            if (e != cudaSuccess) return cuda_fail(e, "tuning the served step");
-            sv->tuned = true;
+    }
+    {
+        // the launch shape follows the work in flight: re-tuned (once per size
+        // class, remembered) whenever the class changes, the graph re-captured
+        // when the shape does
+        int64_t pts = 0;
+        for (const auto &r : sv->slots)
+            if (r) pts += r->req.m;
+        const int n = count_in_flight(sv);
+        if (n > 0) {
+            const auto cls = fricp::size_class(pts, n);
+            if (!sv->tuned || cls != sv->tuned_class) {
+                cudaError_t e = sv->eng.tune(pts, n);
+                if (e == cudaSuccess) e = sv->eng.capture(sv->steps_per_graph);
+                if (e != cudaSuccess) return cuda_fail(e, "tuning the served step");
+                sv->tuned = true;
+                sv->tuned_class = cls;
+            }
         }
     }
     const int graphs = sv->tuned && count_in_flight(sv) > 0 ? (nsteps + sv->steps_per_graph - 1) / sv->steps_per_graph : 0;
