@@ -144,7 +144,7 @@ __device__ __forceinline__ void copy_head(const StepHead *src, StepHead *dst, in
     for (int k = lane; k < W; k += nthreads) d[k] = __ldcg(s + k);
 }
 
-__global__ void __launch_bounds__(kBlock) k_nn_batch(const Slot *__restrict__ slots, const StepHead *heads,
+__global__ void __launch_bounds__(kBlock, 4) k_nn_batch(const Slot *__restrict__ slots, const StepHead *heads,
                                                      const int *__restrict__ tile_slot,
                                                      const int *__restrict__ tile_local, BatchCtl *ctl, int chunk,
                                                      unsigned max_tickets, int order) {
