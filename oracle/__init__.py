@@ -418,7 +418,7 @@ def nu_min_point_to_plane(Qn: np.ndarray, Nq: np.ndarray) -> float:
 # Parameters and results
 # ---------------------------------------------------------------------------
 
-VARIANTS = ("p2p", "p2p_welsch", "p2pl_welsch", "p2pl")
+VARIANTS = ("p2p", "p2p_welsch", "p2pl_welsch", "p2pl", "sym_welsch")
 
 
 @dataclasses.dataclass
@@ -574,12 +574,11 @@ def register_point_to_point(P32, Q32, params: Params, T0=None) -> dict:
 # Point-to-plane (Sec. 5, App. D) and Algorithm 2
 # ---------------------------------------------------------------------------
 
-def plane_gradient(xi: np.ndarray, P: np.ndarray, Nq: np.ndarray) -> np.ndarray:
-    """J_i of Eq. (17) for every source point (App. D). Returns [M, 6].
-
-    B_i(xi) = (R p_i + t - q_i) . n_i, xi = [delta; u], R = exp(delta^),
-    t = ((R - I) u^ delta + delta delta^T u) / |delta|^2.
-    """
+def se3_partials(xi: np.ndarray):
+    """App. D: R = exp(delta^) and the partial derivatives of R and of the
+    translation t(delta, u) = ((R - I) u^ delta + delta delta^T u) / |delta|^2
+    with respect to xi = [delta; u]. Returns (R, dR (list of three 3x3),
+    dt/d delta (3x3, column j), dt/du (3x3))."""
     delta, u = np.asarray(xi[:3], np.float64), np.asarray(xi[3:6], np.float64)
     th2 = float(delta @ delta)
     th = math.sqrt(th2)
@@ -606,9 +605,43 @@ def plane_gradient(xi: np.ndarray, P: np.ndarray, Nq: np.ndarray) -> np.ndarray:
         # (the derivative of 1/|delta|^2 times M delta).
         dt_dd = (Mm + np.outer(delta, u) + D) / th2 - 2.0 / (th2 * th2) * Mm @ np.outer(delta, delta)
         dt_du = ((I - R) @ hat(delta) + np.outer(delta, delta)) / th2
+    return R, dR, dt_dd, dt_du
+
+
+def plane_gradient(xi: np.ndarray, P: np.ndarray, Nq: np.ndarray) -> np.ndarray:
+    """J_i of Eq. (17) for every source point (App. D). Returns [M, 6].
+
+    B_i(xi) = (R p_i + t - q_i) . n_i, xi = [delta; u], R = exp(delta^),
+    t = ((R - I) u^ delta + delta delta^T u) / |delta|^2.
+    """
+    _, dR, dt_dd, dt_du = se3_partials(xi)
     # dB/dR = n p^T, dB/dt = n (App. D)
     Jd = np.stack([np.einsum("ni,ij,nj->n", Nq, dR[j], P) + Nq @ dt_dd[:, j] for j in range(3)], 1)
     Ju = Nq @ dt_du
+    return np.concatenate([Jd, Ju], axis=1)
+
+
+def symmetric_residual(xi: np.ndarray, P: np.ndarray, Qh: np.ndarray, Nq: np.ndarray, Np: np.ndarray):
+    """Residual of the symmetric objective (the extension Sec. 7 proposes):
+    H_i(xi) = (R p_i + t - q_i) . (R np_i + nq_i), the sum of the two surfaces'
+    normals at the pair, the source normal carried by the motion. Returns
+    (H [M], X = R p + t [M,3], the summed normals [M,3])."""
+    T = se3_transform(xi)
+    X = apply(T, P)
+    Ns = Np @ T[:3, :3].T + Nq
+    return np.einsum("nd,nd->n", X - Qh, Ns), X, Ns
+
+
+def symmetric_gradient(xi: np.ndarray, P: np.ndarray, Qh: np.ndarray, Nq: np.ndarray, Np: np.ndarray) -> np.ndarray:
+    """dH_i / dxi of symmetric_residual for every source point, from App. D's
+    partials: d H / d delta_j = (dR_j p + dt/d delta_j) . (R np + nq)
+    + (R p + t - q) . (dR_j np), d H / d u = (dt/du)^T (R np + nq). Returns [M, 6]."""
+    _, dR, dt_dd, dt_du = se3_partials(xi)
+    _, X, Ns = symmetric_residual(xi, P, Qh, Nq, Np)
+    Dv = X - Qh
+    Jd = np.stack([np.einsum("ni,ij,nj->n", Ns, dR[j], P) + Ns @ dt_dd[:, j]
+                   + np.einsum("ni,ij,nj->n", Dv, dR[j], Np) for j in range(3)], 1)
+    Ju = Ns @ dt_du
     return np.concatenate([Jd, Ju], axis=1)
 
 
@@ -616,16 +649,25 @@ def se3_transform(xi) -> np.ndarray:
     return se3_exp(se3_matrix(xi))
 
 
-def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
+def register_point_to_plane(P32, Q32, N32, params: Params, T0=None, Np32=None) -> dict:
     """Algorithm 2 (Welsch point-to-plane ICP with AA). params.variant 'p2pl'
     runs the plain point-to-plane objective of Eq. (15) the same way. Reading:
     psi(x) = x^2, so gamma_i = 1 and the energy is sum H_i^2, and a single stage
     whose iteration cap is max_iters (the caps 6..10 of Sec. 5 belong to the nu
-    stages, which plain point-to-plane does not have)."""
-    robust = params.variant == "p2pl_welsch"
+    stages, which plain point-to-plane does not have).
+
+    params.variant 'sym_welsch' (source normals Np32 required) runs the robust
+    symmetric objective Sec. 7 proposes as future work, read as Alg. 2 with the
+    residual H_i of symmetric_residual in place of Eq. (15)'s: Welsch weights and
+    energy on H_i, the Gauss-Newton system of Eq. (18) with its gradient
+    symmetric_gradient, the same Anderson step, line search and nu stages, and
+    nu_min from the target's statistic of Sec. 5."""
+    sym = params.variant == "sym_welsch"
+    robust = params.variant in ("p2pl_welsch", "sym_welsch")
     P = np.asarray(P32, dtype=np.float64)
     Q = np.asarray(Q32, dtype=np.float64)
     Nr = np.asarray(N32, dtype=np.float64)       # normals used as given
+    Np = np.asarray(Np32, dtype=np.float64) if sym else None
     nz = normalization(P, Q)
     Pn, Qn = nz.fwd(P), nz.fwd(Q)
     cnt = _counters()
@@ -640,12 +682,15 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
         T = se3_transform(xi)
         idx, _, _ = nn(apply(T, Pn))
         n = Nr[idx]
-        B = np.einsum("nd,nd->n", apply(T, Pn) - Qn[idx], n)
+        if sym:
+            B, _, _ = symmetric_residual(xi, Pn, Qn[idx], n, Np)
+        else:
+            B = np.einsum("nd,nd->n", apply(T, Pn) - Qn[idx], n)
         if robust:
             E = float(welsch(B, nu).sum()) if nu is not None else None
         else:
             E = float((B * B).sum())
-        return dict(xi=np.array(xi, dtype=np.float64), idx=idx, B=B, n=n, E=E)
+        return dict(xi=np.array(xi, dtype=np.float64), idx=idx, B=B, n=n, E=E, Qh=Qn[idx])
 
     _, jit_xi = _jitter(params)
 
@@ -658,7 +703,7 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
         """
         xi = ev["xi"]
         gamma = np.exp(-ev["B"] ** 2 / (2.0 * nu * nu)) if robust else np.ones_like(ev["B"])
-        J = plane_gradient(xi, Pn, ev["n"])
+        J = symmetric_gradient(xi, Pn, ev["Qh"], ev["n"], Np) if sym else plane_gradient(xi, Pn, ev["n"])
         A = (J * gamma[:, None]).T @ J
         b = (J * gamma[:, None]).T @ (J @ xi - ev["B"])
         # Reading for points in a plane (Sec. 3: the problem is stated in R^d):
@@ -766,13 +811,15 @@ def register_point_to_plane(P32, Q32, N32, params: Params, T0=None) -> dict:
     return _result(nz, se3_transform(xk), cnt, nu_max, nu_min, E_prev, trace)
 
 
-def register(P32, Q32, params: Params, normals=None, T0=None) -> dict:
+def register(P32, Q32, params: Params, normals=None, T0=None, source_normals=None) -> dict:
     if params.variant in ("p2p", "p2p_welsch"):
         return register_point_to_point(P32, Q32, params, T0)
-    if params.variant in ("p2pl_welsch", "p2pl"):
+    if params.variant in ("p2pl_welsch", "p2pl", "sym_welsch"):
         if normals is None:
             raise ValueError("point-to-plane needs target normals")
-        return register_point_to_plane(P32, Q32, normals, params, T0)
+        if params.variant == "sym_welsch" and source_normals is None:
+            raise ValueError("the symmetric objective needs source normals")
+        return register_point_to_plane(P32, Q32, normals, params, T0, source_normals)
     raise ValueError(params.variant)
 
 

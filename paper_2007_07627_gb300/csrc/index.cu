@@ -653,6 +653,94 @@ __global__ void k_normal_from_cov(Index ix, const double *__restrict__ cov, doub
     out[3 * (size_t)o + 2] = (float)(n[2] * sg);
 }
 
+// Grid-wide form of block_median_pair for large n (the nu_min medians of a
+// whole target): the same eight 8-bit radix passes over the IEEE bit patterns,
+// but each pass's two histograms are built by every block (shared-memory
+// histograms folded into MedianState::hist with one atomic per bin and block)
+// and one block then locates each rank's bin. Counts do not depend on the
+// order of the atomics, so the result is the one block_median_pair gives.
+// Launch order: k_median_init, then for shift = 56, 48, ..., 0 one
+// k_median_hist and one k_median_pick (64 threads); the last pick writes
+// 0.5 * (lo + hi) to *out.
+struct MedianState {
+    unsigned long long prefix[2];
+    int k[2];
+    unsigned int hist[2][256];
+};
+
+__global__ void k_median_init(MedianState *st, int n) {
+    for (int b = threadIdx.x; b < 512; b += blockDim.x) (&st->hist[0][0])[b] = 0u;
+    if (threadIdx.x == 0) {
+        st->prefix[0] = st->prefix[1] = 0ull;
+        st->k[0] = (n - 1) / 2;
+        st->k[1] = n / 2;
+    }
+}
+
+__global__ void k_median_hist(const double *v, int n, MedianState *st, int shift) {
+    __shared__ unsigned int hist[2][256];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int b = threadIdx.x; b < 512; b += blockDim.x) (&hist[0][0])[b] = 0u;
+    __syncthreads();
+    const unsigned long long p0 = st->prefix[0], p1 = st->prefix[1];
+    const unsigned long long mask = (shift == 56) ? 0ull : (~0ull << (shift + 8));
+    // every lane runs every round (the peer match is warp-wide)
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        unsigned long long key = ~0ull;
+        if (i < n) key = (unsigned long long)__double_as_longlong(__ldcg(v + i));
+        const int bin = (int)((key >> shift) & 255ull);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const bool match = i < n && (key & mask) == (r ? p1 : p0);
+            const unsigned peers = __match_any_sync(FULL, match ? bin : -1);
+            if (match && lane == __ffs(peers) - 1) atomicAdd(&hist[r][bin], (unsigned)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 512; b += blockDim.x) {
+        const unsigned c = (&hist[0][0])[b];
+        if (c) atomicAdd(&st->hist[0][0] + b, c);
+    }
+}
+
+__global__ void __launch_bounds__(64) k_median_pick(MedianState *st, int shift, double *out) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < 2) {   // warp r finds the bin holding its rank (as block_median_pair)
+        unsigned c[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            c[q] = st->hist[w][8 * lane + q];
+            sum += c[q];
+        }
+        unsigned incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const unsigned excl = incl - sum;
+        const unsigned k = (unsigned)st->k[w];
+        const unsigned owner = __ballot_sync(FULL, excl <= k && k < incl);
+        if (lane == __ffs(owner) - 1) {
+            unsigned cum = excl;
+            int q = 0;
+            for (; q < 7; ++q) {
+                if (cum + c[q] > k) break;
+                cum += c[q];
+            }
+            st->k[w] = (int)(k - cum);
+            st->prefix[w] |= (unsigned long long)(8 * lane + q) << shift;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 512; b += blockDim.x) (&st->hist[0][0])[b] = 0u;   // for the next pass
+    if (shift == 0 && threadIdx.x == 0)
+        *out = 0.5 * (__longlong_as_double((long long)st->prefix[0]) + __longlong_as_double((long long)st->prefix[1]));
+}
+
 __global__ void k_median(const double *v, int n, double *out) {
     double a, b;
     block_median_pair(v, n, &a, &b);
@@ -835,7 +923,9 @@ cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
         return cudaSuccess;
     }
     double *sd = nullptr, *sh = nullptr, *out = nullptr;
+    MedianState *mst = nullptr;
     cudaError_t e = cudaMallocAsync(&sd, sizeof(double) * t->n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&mst, sizeof(MedianState), s);
     if (e == cudaSuccess && t->has_normals) e = cudaMallocAsync(&sh, sizeof(double) * t->n, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&out, 3 * sizeof(double), s);
     int *flag = reinterpret_cast<int *>(out + 2);
@@ -848,11 +938,16 @@ cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
         const int64_t blocks = std::min<int64_t>((t->n + kKnnBlock / 32 - 1) / (kKnnBlock / 32),
                                                  (int64_t)(sms > 0 ? sms : 152) * 16);
         k_knn6_stats<<<(unsigned)blocks, kKnnBlock, 0, s>>>(ix, sd, sh, flag);
-        k_median<<<1, 1024, 0, s>>>(sd, (int)t->n, out);
-        counters().launches += 2;
-        if (sh) {
-            k_median<<<1, 1024, 0, s>>>(sh, (int)t->n, out + 1);
-            counters().launches += 1;
+        counters().launches += 1;
+        const unsigned mblocks = (unsigned)std::min<int64_t>((t->n + 255) / 256, (int64_t)(sms > 0 ? sms : 152) * 4);
+        for (int which = 0; which < (sh ? 2 : 1); ++which) {
+            const double *v = which ? sh : sd;
+            k_median_init<<<1, 256, 0, s>>>(mst, (int)t->n);
+            for (int shift = 56; shift >= 0; shift -= 8) {
+                k_median_hist<<<mblocks, 256, 0, s>>>(v, (int)t->n, mst, shift);
+                k_median_pick<<<1, 64, 0, s>>>(mst, shift, out + which);
+            }
+            counters().launches += 17;
         }
         double h[3] = {0.0, 0.0, 0.0};
         e = cudaMemcpyAsync(h, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -869,6 +964,7 @@ cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
     if (sd) cudaFreeAsync(sd, s);
     if (sh) cudaFreeAsync(sh, s);
     if (out) cudaFreeAsync(out, s);
+    if (mst) cudaFreeAsync(mst, s);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e;
 }

@@ -36,6 +36,9 @@ class Pair:
     P, Q: float32 [M,3], [N,3]. normals: float32 [N,3] unit normals of Q (or None).
     R_gt, t_gt: float64 ground-truth motion taking P onto Q (x -> R_gt x + t_gt).
     diag: bounding-box diagonal of the clean target surface.
+    src_normals: float32 [M,3] unit normals of P: the surface normal at each sampled
+    point moved with the source (noise moves positions only); an outlier gets a
+    random unit normal.
     """
     P: np.ndarray
     Q: np.ndarray
@@ -44,6 +47,7 @@ class Pair:
     t_gt: np.ndarray
     diag: float
     name: str = ""
+    src_normals: np.ndarray | None = None
 
     @property
     def M(self) -> int:
@@ -195,17 +199,23 @@ def _assemble(g, draw, M, N, overlap, noise, outliers, max_angle, dim_crop, name
     Q, nQ = _fill(draw, N, keep_T, g)
     diag = float(np.linalg.norm(Q.max(0) - Q.min(0)))
     n_out = int(round(outliers * M))
-    S, _ = _fill(draw, M - n_out, keep_S, g)
+    S, nS = _fill(draw, M - n_out, keep_S, g)
     S = S + noise * diag * g.standard_normal(S.shape)
     if n_out:
         lo, hi = S.min(0), S.max(0)
         S = np.concatenate([S, lo + (hi - lo) * g.random((n_out, 3))])
-    S = S[g.permutation(S.shape[0])]
+        nS = np.concatenate([nS, np.zeros((n_out, 3))])
+    perm = g.permutation(S.shape[0])
+    S, nS = S[perm], nS[perm]
     R_s, t_s = random_rigid(g, max_angle, 0.1 * diag)
     P = S @ R_s.T + t_s
+    if n_out:   # drawn after everything above, so P and Q do not depend on it
+        out = perm >= M - n_out
+        nS[out] = _unit(g.standard_normal((int(out.sum()), 3)))
+    nP = nS @ R_s.T
     return Pair(P=P.astype(np.float32), Q=Q.astype(np.float32),
                 normals=nQ.astype(np.float32), R_gt=R_s.T.copy(),
-                t_gt=-(R_s.T @ t_s), diag=diag, name=name)
+                t_gt=-(R_s.T @ t_s), diag=diag, name=name, src_normals=nP.astype(np.float32))
 
 
 def torus_pair(seed, M=2000, N=2000, overlap=1.0, noise=0.002, outliers=0.0,

@@ -695,3 +695,75 @@ def test_registration_with_kdtree_correspondences_equals_bruteforce():
             assert a[key] == b[key]
         assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["t"], b["t"])
         assert np.array_equal(a["trace"], b["trace"])
+
+
+# --------------------------------------------------------------------------
+# Robust symmetric objective (Sec. 7's proposed extension), read as Alg. 2 on
+# H_i = (R p_i + t - q_i) . (R np_i + nq_i).
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("delta_scale", [0.0, 1e-8, 0.3, 1.2])
+def test_symmetric_gradient_central_differences(delta_scale):
+    g = np.random.default_rng(31)
+    P = g.standard_normal((50, 3))
+    Qh = g.standard_normal((50, 3))
+    Nq = g.standard_normal((50, 3))
+    Nq /= np.linalg.norm(Nq, axis=1, keepdims=True)
+    Np = g.standard_normal((50, 3))
+    Np /= np.linalg.norm(Np, axis=1, keepdims=True)
+    d = g.standard_normal(3)
+    u = g.standard_normal(3) if delta_scale else np.zeros(3)   # App. D's delta=0 case is exact at u=0
+    xi = np.concatenate([delta_scale * d / np.linalg.norm(d), u])
+    J = oracle.symmetric_gradient(xi, P, Qh, Nq, Np)
+    h = 1e-6
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        Hp, _, _ = oracle.symmetric_residual(xi + e, P, Qh, Nq, Np)
+        Hm, _, _ = oracle.symmetric_residual(xi - e, P, Qh, Nq, Np)
+        fd = (Hp - Hm) / (2 * h)
+        assert np.abs(J[:, k] - fd).max() <= 1e-7 * max(1.0, np.abs(fd).max()), k
+
+
+def test_symmetric_objective_without_source_normals_is_point_to_plane():
+    """With every source normal zero, H_i is the point-to-plane residual of
+    Eq. (15), its gradient that of App. D, and the registration is Alg. 2's, bit
+    for bit (counters, transform, energy trace)."""
+    from paper_2007_07627_gb300 import synth
+    pair = synth.config_pair(3, 0.01)
+    a = oracle.register(pair.P, pair.Q, oracle.Params(variant="p2pl_welsch"), normals=pair.normals)
+    b = oracle.register(pair.P, pair.Q, oracle.Params(variant="sym_welsch"), normals=pair.normals,
+                        source_normals=np.zeros_like(pair.P))
+    for key in ("iterations", "corr_passes", "reverts", "line_search_trials", "stages"):
+        assert a[key] == b[key], key
+    assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["t"], b["t"])
+    assert np.array_equal(a["trace"], b["trace"])
+
+
+def test_symmetric_objective_recovers_an_exact_copy():
+    """Target = a surface sample with its normals; source = the same points and
+    normals under a known rigid motion: the registration returns the inverse
+    motion and the energy goes to zero."""
+    from paper_2007_07627_gb300 import synth
+    pair = synth.ellipsoid_pair(synth.CONFIG_SEEDS[3], M=3000, N=3000, overlap=1.0, noise=0.0, outliers=0.0,
+                                max_angle=0.0)
+    Q, N = pair.Q.astype(np.float64), pair.normals.astype(np.float64)
+    g = np.random.default_rng(32)
+    R0 = _rot(g, 0.25)
+    t0 = 0.03 * g.standard_normal(3)
+    P = (Q @ R0.T + t0).astype(np.float32)
+    Np = (N @ R0.T).astype(np.float32)
+    r = oracle.register(P, pair.Q, oracle.Params(variant="sym_welsch"), normals=pair.normals, source_normals=Np)
+    assert r["status"] == "ok"
+    assert np.abs(r["R"] - R0.T).max() < 1e-6
+    assert np.abs(r["t"] + R0.T @ t0).max() < 1e-6
+
+
+def test_symmetric_objective_accepted_energy_is_monotone_within_stages():
+    from paper_2007_07627_gb300 import synth
+    pair = synth.config_pair(3, 0.01)
+    r = oracle.register(pair.P, pair.Q, oracle.Params(variant="sym_welsch", nu_max=0.05, nu_min=0.05),
+                        normals=pair.normals, source_normals=pair.src_normals)
+    tr = np.asarray(r["trace"])
+    assert r["stages"] == 1 and len(tr) > 3
+    assert np.all(np.diff(tr) <= 1e-12 * np.abs(tr[:-1]))
