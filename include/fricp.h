@@ -63,8 +63,11 @@ typedef enum {
     FRICP_P2P_AA = 0,
     FRICP_P2P_WELSCH_AA = 1,
     FRICP_P2PL_WELSCH_AA = 2,
-    FRICP_P2PL_AA = 3        /* plain point-to-plane ICP (Eq. 15) solved like Alg. 2 with psi(x) = x^2:
+    FRICP_P2PL_AA = 3,       /* plain point-to-plane ICP (Eq. 15) solved like Alg. 2 with psi(x) = x^2:
                                 weights 1, energy sum H_i^2, one stage capped by max_iters */
+    FRICP_SYM_WELSCH_AA = 4  /* Welsch-robust symmetric objective, the extension Sec. 7 proposes: Alg. 2
+                                on H_i = (R p_i + t - q_i) . (R np_i + nq_i), the two surfaces' normals
+                                summed at each pair (needs source normals: fricp_register_symmetric) */
 } fricp_variant;
 
 /* Arithmetic of the correspondence search and the per-point terms. The sums,
@@ -237,6 +240,26 @@ fricp_status fricp_register_recorded(const fricp_target *target, const float *p_
                                      void *stream, fricp_result *out, double *trace,
                                      int32_t trace_capacity, fricp_step_record *steps,
                                      int32_t steps_capacity, int32_t *steps_len);
+
+/* The Welsch-robust symmetric objective, the extension the paper proposes in
+ * Sec. 7 (replacing symmetric ICP's l2 target with a robust metric): Alg. 2
+ * (Gauss-Newton on the App. D parameterisation, Anderson step, line search,
+ * nu stages) on the residual H_i = (R p_i + t - q_i) . (R np_i + nq_i) of each
+ * source point and its closest target point, where np_i is the source point's
+ * unit normal (moved with the source) and nq_i the target's. Welsch weights and
+ * energy on H_i; nu_max = 3 x median |H_i| at T0, nu_min = H_Q / 6 as for
+ * point-to-plane (Sec. 5). params->variant must be FRICP_SYM_WELSCH_AA; the
+ * target needs normals. p_normals: float32 [m][3] in p_xyz's memory space,
+ * each a unit normal (within 1e-3) or zero for a point without a normal, whose
+ * residual is then the point-to-plane one (with every np_i zero the
+ * registration is FRICP_P2PL_WELSCH_AA's, bit for bit). Other arguments as fricp_register_recorded (steps may be NULL with
+ * steps_capacity 0). The batched and served engines do not run this variant.
+ * Errors: as fricp_register; EINVAL for a source normal neither zero nor unit. */
+fricp_status fricp_register_symmetric(const fricp_target *target, const float *p_xyz, const float *p_normals,
+                                      int64_t m, int32_t on_device, const double *T0,
+                                      const fricp_params *params, void *stream, fricp_result *out,
+                                      double *trace, int32_t trace_capacity, fricp_step_record *steps,
+                                      int32_t steps_capacity, int32_t *steps_len);
 
 /* Batched registration (no counterpart in the paper, which registers one pair
  * at a time): npairs independent registrations -- pair i registers p_xyz[i]

@@ -22,8 +22,9 @@ __all__ = [
     "closest_points", "eval_pass", "target_nu_min", "version", "counters",
 ]
 
-P2P_AA, P2P_WELSCH_AA, P2PL_WELSCH_AA, P2PL_AA = 0, 1, 2, 3
-VARIANTS = {"p2p": P2P_AA, "p2p_welsch": P2P_WELSCH_AA, "p2pl_welsch": P2PL_WELSCH_AA, "p2pl": P2PL_AA}
+P2P_AA, P2P_WELSCH_AA, P2PL_WELSCH_AA, P2PL_AA, SYM_WELSCH_AA = 0, 1, 2, 3, 4
+VARIANTS = {"p2p": P2P_AA, "p2p_welsch": P2P_WELSCH_AA, "p2pl_welsch": P2PL_WELSCH_AA, "p2pl": P2PL_AA,
+            "sym_welsch": SYM_WELSCH_AA}
 PREC_FP64, PREC_FP32, PREC_FP16_STORAGE = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "fp16": PREC_FP16_STORAGE}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EDEGENERATE", 6: "EUNSUPPORTED",
@@ -94,6 +95,9 @@ def lib() -> ctypes.CDLL:
     L.fricp_register.argtypes = [vp, vp, i64, i32, dp, ctypes.POINTER(Params), vp, ctypes.POINTER(Result), dp, i32]
     L.fricp_register_recorded.argtypes = [vp, vp, i64, i32, dp, ctypes.POINTER(Params), vp, ctypes.POINTER(Result),
                                           dp, i32, ctypes.POINTER(StepRecord), i32, ctypes.POINTER(i32)]
+    L.fricp_register_symmetric.argtypes = [vp, vp, vp, i64, i32, dp, ctypes.POINTER(Params), vp,
+                                           ctypes.POINTER(Result), dp, i32, ctypes.POINTER(StepRecord), i32,
+                                           ctypes.POINTER(i32)]
     L.fricp_closest_points.argtypes = [vp, vp, i64, dp, vp, vp, vp]
     L.fricp_eval_pass.argtypes = [vp, vp, i64, i32, i32, dp, dbl, dbl, dp, vp, dp]
     L.fricp_target_nu_min.argtypes = [vp, i32, dbl, vp, dp]
@@ -117,7 +121,7 @@ def lib() -> ctypes.CDLL:
     L.fricp_server_destroy.argtypes = [vp]
     L.fricp_batch_last_shape.restype = None
     for name in ("fricp_params_default", "fricp_target_create", "fricp_target_destroy", "fricp_register",
-                 "fricp_register_recorded",
+                 "fricp_register_recorded", "fricp_register_symmetric",
                  "fricp_closest_points", "fricp_eval_pass", "fricp_target_nu_min", "fricp_batch_register",
                  "fricp_server_create", "fricp_server_submit", "fricp_server_step", "fricp_server_poll",
                  "fricp_server_destroy", "fricp_estimate_normals", "fricp_batch_set_shape"):
@@ -254,10 +258,12 @@ def register(target: Target, p, T0=None, params: Params | None = None, stream=No
 
 
 def register_recorded(target: Target, p, T0=None, params: Params | None = None, stream=None,
-                      trace_capacity: int = 0, steps_capacity: int = 4096, variant=None):
+                      trace_capacity: int = 0, steps_capacity: int = 4096, variant=None, source_normals=None):
     """fricp_register_recorded: as register(), plus one record per
     correspondence pass (a list of dicts: step, phase, revert, accepted, stage,
-    done, nu, E, E_prev, T (4x4, normalised), xi (6), result (12 or 6))."""
+    done, nu, E, E_prev, T (4x4, normalised), xi (6), result (12 or 6)).
+    With source_normals (float32 [m,3], p's memory space) it calls
+    fricp_register_symmetric (params.variant must be "sym_welsch")."""
     if params is None:
         params = params_default(variant if variant is not None else P2P_WELSCH_AA)
     pp, m, dev, pk = _points(p)
@@ -267,9 +273,17 @@ def register_recorded(target: Target, p, T0=None, params: Params | None = None, 
     r = Result()
     recs = (StepRecord * max(steps_capacity, 1))()
     n = ctypes.c_int32()
-    _check(lib().fricp_register_recorded(target.handle, pp, m, dev, Tp, ctypes.byref(params), _stream(stream),
-                                         ctypes.byref(r), tp, int(trace_capacity), recs, int(steps_capacity),
-                                         ctypes.byref(n)))
+    if source_normals is None:
+        _check(lib().fricp_register_recorded(target.handle, pp, m, dev, Tp, ctypes.byref(params), _stream(stream),
+                                             ctypes.byref(r), tp, int(trace_capacity), recs, int(steps_capacity),
+                                             ctypes.byref(n)))
+    else:
+        npp, nm, ndev, nk = _points(source_normals)
+        if nm != m or ndev != dev:
+            raise ValueError("source normals must match p in size and memory space")
+        _check(lib().fricp_register_symmetric(target.handle, pp, npp, m, dev, Tp, ctypes.byref(params),
+                                              _stream(stream), ctypes.byref(r), tp, int(trace_capacity), recs,
+                                              int(steps_capacity), ctypes.byref(n)))
     steps = []
     for k in range(n.value):
         x = recs[k]
@@ -280,6 +294,17 @@ def register_recorded(target: Target, p, T0=None, params: Params | None = None, 
                           done=x.done, nu=x.nu, E=x.E, E_prev=x.E_prev, T=T, xi=np.array(x.xi[:]),
                           result=np.array(x.result[:])))
     return _result(r, trace if trace_capacity > 0 else None), steps
+
+
+def register_symmetric(target: Target, p, source_normals, T0=None, params: Params | None = None, stream=None,
+                       trace_capacity: int = 0) -> dict:
+    """fricp_register_symmetric: the Welsch-robust symmetric objective (Sec. 7's
+    proposed extension of Alg. 2) with the source's unit normals."""
+    if params is None:
+        params = params_default(SYM_WELSCH_AA)
+    res, _ = register_recorded(target, p, T0=T0, params=params, stream=stream, trace_capacity=trace_capacity,
+                               steps_capacity=0, source_normals=source_normals)
+    return res
 
 
 def batch_register(targets, sources, params=None, T0=None, stream=None, trace_capacity: int = 0) -> list:

@@ -139,7 +139,7 @@ const char *fricp_last_error(void) { return g_err.c_str(); }
 
 fricp_status fricp_params_default(int32_t variant, fricp_params *out) {
     if (out == nullptr) return fail(FRICP_EINVAL, "out is NULL");
-    if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_AA) return fail(FRICP_EINVAL, "unknown variant");
+    if (variant < FRICP_P2P_AA || variant > FRICP_SYM_WELSCH_AA) return fail(FRICP_EINVAL, "unknown variant");
     std::memset(out, 0, sizeof(*out));
     out->variant = variant;
     out->anderson_m = 5;
@@ -279,9 +279,9 @@ fricp_status fricp_closest_points(const fricp_target *t, const float *p_xyz, int
 namespace {
 
 // fricp_register, with per-pass records when steps_capacity > 0.
-fricp_status register_impl(const fricp_target *t, const float *p_xyz, int64_t m, int32_t on_device,
-                           const double *T0, const fricp_params *params, void *stream, fricp_result *out,
-                           double *trace, int32_t trace_capacity, fricp_step_record *steps,
+fricp_status register_impl(const fricp_target *t, const float *p_xyz, const float *p_normals, int64_t m,
+                           int32_t on_device, const double *T0, const fricp_params *params, void *stream,
+                           fricp_result *out, double *trace, int32_t trace_capacity, fricp_step_record *steps,
                            int32_t steps_capacity, int32_t *steps_len) {
     const auto wall0 = std::chrono::steady_clock::now();
     if (!t || !p_xyz || !params || !out) return fail(FRICP_EINVAL, "NULL argument");
@@ -294,15 +294,23 @@ fricp_status register_impl(const fricp_target *t, const float *p_xyz, int64_t m,
     const fricp_params prm = *params;
     if (fricp::variant_p2pl(prm.variant) && !t->d.has_normals)
         return fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");
+    if (fricp::variant_sym(prm.variant) && !p_normals)
+        return fail(FRICP_EUNSUPPORTED, "the symmetric objective needs source normals (fricp_register_symmetric)");
+    if (!fricp::variant_sym(prm.variant) && p_normals)
+        return fail(FRICP_EINVAL, "source normals are used by FRICP_SYM_WELSCH_AA only");
     if (T0)
         for (int i = 0; i < 16; ++i)
             if (!std::isfinite(T0[i])) return fail(FRICP_EINVAL, "T0 has NaN or Inf");
     std::memset(out, 0, sizeof(*out));
     Ordered ord(stream);
     const cudaStream_t s = ord.work;
-    DevInput p;
+    DevInput p, pn;
     st = stage_input(p_xyz, m, on_device, s, &p, "p_xyz");
     if (st != FRICP_OK) return st;
+    if (p_normals) {
+        st = stage_input(p_normals, m, on_device, s, &pn, "p_normals");
+        if (st != FRICP_OK) return st;
+    }
 
     const int ntiles = (int)((m + fricp::kBlock - 1) / fricp::kBlock);
     const bool robust = fricp::variant_robust(prm.variant);
@@ -317,11 +325,16 @@ fricp_status register_impl(const fricp_target *t, const float *p_xyz, int64_t m,
     DevBuf<fricp_step_record> rec;
     if (steps_capacity > 0 && rec.alloc(steps_capacity, s) != cudaSuccess)
         return fail(FRICP_ENOMEM, "device allocation for the step records");
+    DevBuf<float4> src_nrm;
+    if (p_normals && src_nrm.alloc(m, s) != cudaSuccess)
+        return fail(FRICP_ENOMEM, "device allocation for the source normals");
     float plo[3], phi[3];
     int bad = 0;
-    cudaError_t e = fricp::prepare_source(p.ptr, m, s, src.p, plo, phi, &bad);
+    cudaError_t e = fricp::prepare_source(p.ptr, m, s, src.p, plo, phi, &bad, p_normals ? pn.ptr : nullptr,
+                                          p_normals ? src_nrm.p : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "preparing the source");
-    if (bad) return fail(FRICP_EINVAL, "p_xyz has NaN or Inf");
+    if (bad) return fail(FRICP_EINVAL, p_normals ? "p_xyz has NaN or Inf, or p_normals a non-unit normal"
+                                                 : "p_xyz has NaN or Inf");
 
     double scale, c[3];
     PairState h;
@@ -341,6 +354,7 @@ fricp_status register_impl(const fricp_target *t, const float *p_xyz, int64_t m,
     a.st = st_dev.p;
     a.ix = fricp::make_index(t->d);
     a.src = src.p;
+    a.src_nrm = p_normals ? src_nrm.p : nullptr;
     a.prev = prev.p;
     a.partial = partial.p;
     a.resid = resid.p;
@@ -349,7 +363,7 @@ fricp_status register_impl(const fricp_target *t, const float *p_xyz, int64_t m,
     double pass_ms = 0.0, search_ms = 0.0;
     st = run_steps(a, prm.variant, ntiles, prm, s, st_dev.p, &leak, &pass_ms, &search_ms);
     if (leak) {
-        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = rec.leak = true;
+        src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = rec.leak = src_nrm.leak = true;
         p.owned = nullptr;
     }
     if (st != FRICP_OK && st != FRICP_ETIMEOUT) return st;
@@ -388,15 +402,26 @@ extern "C" {
 fricp_status fricp_register(const fricp_target *t, const float *p_xyz, int64_t m, int32_t on_device,
                             const double *T0, const fricp_params *params, void *stream, fricp_result *out,
                             double *trace, int32_t trace_capacity) {
-    return register_impl(t, p_xyz, m, on_device, T0, params, stream, out, trace, trace_capacity, nullptr, 0,
-                         nullptr);
+    return register_impl(t, p_xyz, nullptr, m, on_device, T0, params, stream, out, trace, trace_capacity, nullptr,
+                         0, nullptr);
 }
 
 fricp_status fricp_register_recorded(const fricp_target *t, const float *p_xyz, int64_t m, int32_t on_device,
                                      const double *T0, const fricp_params *params, void *stream,
                                      fricp_result *out, double *trace, int32_t trace_capacity,
                                      fricp_step_record *steps, int32_t steps_capacity, int32_t *steps_len) {
-    return register_impl(t, p_xyz, m, on_device, T0, params, stream, out, trace, trace_capacity, steps,
+    return register_impl(t, p_xyz, nullptr, m, on_device, T0, params, stream, out, trace, trace_capacity, steps,
+                         steps_capacity, steps_len);
+}
+
+fricp_status fricp_register_symmetric(const fricp_target *t, const float *p_xyz, const float *p_normals, int64_t m,
+                                      int32_t on_device, const double *T0, const fricp_params *params,
+                                      void *stream, fricp_result *out, double *trace, int32_t trace_capacity,
+                                      fricp_step_record *steps, int32_t steps_capacity, int32_t *steps_len) {
+    if (!p_normals) return fail(FRICP_EINVAL, "NULL argument");
+    if (params && params->variant != FRICP_SYM_WELSCH_AA)
+        return fail(FRICP_EINVAL, "fricp_register_symmetric runs FRICP_SYM_WELSCH_AA");
+    return register_impl(t, p_xyz, p_normals, m, on_device, T0, params, stream, out, trace, trace_capacity, steps,
                          steps_capacity, steps_len);
 }
 
@@ -405,6 +430,8 @@ fricp_status fricp_eval_pass(const fricp_target *t, const float *p_xyz, int64_t 
                              const double *center, void *stream, double *out) {
     if (!t || !p_xyz || !T_normalized || !out) return fail(FRICP_EINVAL, "NULL argument");
     if (m < 1 || m > (int64_t)1 << 30) return fail(FRICP_EINVAL, "m must be in 1..2^30");
+    if (variant == FRICP_SYM_WELSCH_AA)
+        return fail(FRICP_EUNSUPPORTED, "the symmetric objective needs source normals (fricp_register_symmetric)");
     if (variant < FRICP_P2P_AA || variant > FRICP_P2PL_AA) return fail(FRICP_EINVAL, "unknown variant");
     if (fricp::variant_p2pl(variant) && !t->d.has_normals)
         return fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");

@@ -598,6 +598,8 @@ fricp_status check_pair(const fricp_target *t, const float *p, int64_t m, const 
     if (m < 1 || m > (int64_t)1 << 30) return fail(FRICP_EINVAL, "m must be in 1..2^30");
     fricp_status st = check_params(prm);
     if (st != FRICP_OK) return st;
+    if (fricp::variant_sym(prm->variant))
+        return fail(FRICP_EUNSUPPORTED, "the symmetric objective needs source normals: fricp_register_symmetric");
     if (fricp::variant_p2pl(prm->variant) && !fricp::target_dev(t)->has_normals)
         return fail(FRICP_EUNSUPPORTED, "point-to-plane needs target normals");
     if (T0)

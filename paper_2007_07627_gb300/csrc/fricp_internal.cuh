@@ -50,8 +50,15 @@ enum Prec : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_FP16 = 2 };
 
 // Variant families: point-to-plane (the Alg. 2 scheme, 28 sums) and robust
 // (Welsch weights and nu stages).
-__host__ __device__ inline bool variant_p2pl(int v) { return v == FRICP_P2PL_WELSCH_AA || v == FRICP_P2PL_AA; }
-__host__ __device__ inline bool variant_robust(int v) { return v == FRICP_P2P_WELSCH_AA || v == FRICP_P2PL_WELSCH_AA; }
+__host__ __device__ inline bool variant_p2pl(int v) {
+    return v == FRICP_P2PL_WELSCH_AA || v == FRICP_P2PL_AA || v == FRICP_SYM_WELSCH_AA;
+}
+__host__ __device__ inline bool variant_robust(int v) {
+    return v == FRICP_P2P_WELSCH_AA || v == FRICP_P2PL_WELSCH_AA || v == FRICP_SYM_WELSCH_AA;
+}
+// The symmetric objective: the point-to-plane scheme on a residual that also
+// carries the source point's normal.
+__host__ __device__ inline bool variant_sym(int v) { return v == FRICP_SYM_WELSCH_AA; }
 
 struct Index {
     const float4 *pts;
@@ -141,6 +148,7 @@ struct StepArgs {
     PairState *st;
     Index ix;
     const float4 *src;     // M sorted source points
+    const float4 *src_nrm = nullptr;   // M source normals in the same order (symmetric objective), or null
     int *prev;             // M: correspondence (sorted target index) of the last pass, -1 if none;
                            //    the search kernels overwrite it with this pass's correspondence
     double *partial;       // ntiles * kMaxSums
@@ -965,8 +973,12 @@ cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s);
 cudaError_t estimate_normals(const TargetDev *t, int k, const double viewpoint[3], float *out_dev, cudaStream_t s,
                              int *overflow_out);
 cudaError_t build_fp16_storage(TargetDev *t, cudaStream_t s);
+// Source points in Morton order (and, when n_dev is given, their normals in the
+// same order into nrm_out; a normal that is neither zero nor unit length within
+// 1e-3 counts as bad input).
 cudaError_t prepare_source(const float *p_dev, int64_t m, cudaStream_t s, float4 *src_out,
-                           float lo[3], float hi[3], int *bad_input);
+                           float lo[3], float hi[3], int *bad_input, const float *n_dev = nullptr,
+                           float4 *nrm_out = nullptr);
 cudaError_t launch_closest(const TargetDev *t, const float *p_dev, int64_t m, const double T[12],
                            int64_t *idx, double *d2, cudaStream_t s);
 // One device step: the closest-point search kernel (query tiles, or one query

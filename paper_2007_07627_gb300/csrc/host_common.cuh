@@ -64,7 +64,7 @@ inline bool host_finite(const float *x, int64_t n3) {
 }
 
 inline fricp_status check_params(const fricp_params *p) {
-    if (p->variant < FRICP_P2P_AA || p->variant > FRICP_P2PL_AA) return fail(FRICP_EINVAL, "unknown variant");
+    if (p->variant < FRICP_P2P_AA || p->variant > FRICP_SYM_WELSCH_AA) return fail(FRICP_EINVAL, "unknown variant");
     if (p->anderson_m < 0 || p->anderson_m > fricp::kMaxM) return fail(FRICP_EINVAL, "anderson_m must be in 0..5");
     if (p->max_iters < 1 || p->p2pl_iters_first < 1 || p->p2pl_iters_cap < p->p2pl_iters_first)
         return fail(FRICP_EINVAL, "iteration caps must be >= 1 and cap >= first");

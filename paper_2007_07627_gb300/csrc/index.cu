@@ -30,7 +30,7 @@ struct BoxPartial {
 // Per-block min/max/sum in a fixed order; flags NaN/Inf coordinates and normals
 // that are not unit length within 1e-3.
 __global__ void k_box_partial(const float *__restrict__ x, const float *__restrict__ nrm, int64_t n,
-                              BoxPartial *out) {
+                              BoxPartial *out, int zero_normals_ok) {
     __shared__ float slo[3][kRedBlock], shi[3][kRedBlock];
     __shared__ double ssum[3][kRedBlock];
     __shared__ int sbad;
@@ -50,7 +50,7 @@ __global__ void k_box_partial(const float *__restrict__ x, const float *__restri
         if (nrm != nullptr) {
             const double a0 = nrm[3 * i], a1 = nrm[3 * i + 1], a2 = nrm[3 * i + 2];
             const double l2 = a0 * a0 + a1 * a1 + a2 * a2;
-            if (!(fabs(l2 - 1.0) <= 2e-3)) bad = 1;
+            if (!(fabs(l2 - 1.0) <= 2e-3) && !(zero_normals_ok && l2 == 0.0)) bad = 1;
         }
     }
     __syncthreads();
@@ -753,13 +753,14 @@ struct BoxResult {
     int bad;
 };
 
-cudaError_t reduce_box(const float *x, const float *nrm, int64_t n, cudaStream_t s, BoxResult *res) {
+cudaError_t reduce_box(const float *x, const float *nrm, int64_t n, cudaStream_t s, BoxResult *res,
+                       int zero_normals_ok = 0) {
     int nb = (int)std::min<int64_t>((n + kRedBlock - 1) / kRedBlock, 1024);
     if (nb < 1) nb = 1;
     BoxPartial *parts = nullptr;
     cudaError_t e = cudaMallocAsync(&parts, sizeof(BoxPartial) * (nb + 1), s);
     if (e != cudaSuccess) return e;
-    k_box_partial<<<nb, kRedBlock, 0, s>>>(x, nrm, n, parts);
+    k_box_partial<<<nb, kRedBlock, 0, s>>>(x, nrm, n, parts, zero_normals_ok);
     k_box_final<<<1, kRedBlock, 0, s>>>(parts, nb, parts + nb);
     counters().launches += 2;
     BoxPartial h;
@@ -1001,9 +1002,9 @@ cudaError_t estimate_normals(const TargetDev *t, int k, const double viewpoint[3
 }
 
 cudaError_t prepare_source(const float *p_dev, int64_t m, cudaStream_t s, float4 *src_out, float lo[3],
-                           float hi[3], int *bad_input) {
+                           float hi[3], int *bad_input, const float *n_dev, float4 *nrm_out) {
     BoxResult bx;
-    cudaError_t e = reduce_box(p_dev, nullptr, m, s, &bx);
+    cudaError_t e = reduce_box(p_dev, n_dev, m, s, &bx, 1);   // a zero source normal: no normal at that point
     if (e != cudaSuccess) return e;
     *bad_input = bx.bad;
     if (bx.bad) return cudaSuccess;
@@ -1014,7 +1015,7 @@ cudaError_t prepare_source(const float *p_dev, int64_t m, cudaStream_t s, float4
     int *order = nullptr;
     e = morton_order(p_dev, m, bx, s, &order);
     if (e != cudaSuccess) return e;
-    k_gather<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p_dev, nullptr, order, m, src_out, nullptr);
+    k_gather<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p_dev, n_dev, order, m, src_out, nrm_out);
     counters().launches += 1;
     e = cudaGetLastError();
     cudaFreeAsync(order, s);

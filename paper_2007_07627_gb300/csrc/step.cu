@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_accum(StepArgs a) {
     if (threadIdx.x == 0) load_head(a.st, h);
     __syncthreads();
     if (h.done) return;
-    if (accum_tile<VAR, PREC>(h, a.st, a.ix, a.src, a.prev, a.resid, a.partial, blockIdx.x, gridDim.x, red, &s_last))
+    if (accum_tile<VAR, PREC>(h, a.st, a.ix, a.src, a.prev, a.resid, a.partial, blockIdx.x, gridDim.x, red, &s_last,
+                              a.src_nrm))
         finish_pass<K>(h, a.st, a.partial, gridDim.x, a.resid, a.trace, sS, red);
 }
 

@@ -214,7 +214,8 @@ __device__ __forceinline__ bool search_tile(const Index &ix, const float4 *src, 
 // the sums.
 template <int VAR, int PREC>
 __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, const float4 *src, const int *prev,
-                                            double *resid, int i, double (&acc)[VAR ? kSumsP2PL : kSumsP2P]) {
+                                            double *resid, int i, double (&acc)[VAR ? kSumsP2PL : kSumsP2P],
+                                            const float4 *src_nrm = nullptr) {
     const float4 p = __ldg(src + i);
     const int j = prev[i];
     const float4 q = target_point<PREC>(ix, j);
@@ -251,7 +252,18 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
                 for (int v = 0; v < 3; ++v) acc[7 + 3 * u + v] = (double)(w * pt[u] * qt[v]);
             acc[16] = psi;
         } else {
-            const float4 nv = __ldg(ix.nrm + j);
+            float4 nv = __ldg(ix.nrm + j);
+            float rn[3] = {0.0f, 0.0f, 0.0f};
+            if (src_nrm != nullptr && fricp::variant_sym(h.variant)) {
+                // symmetric objective: the pair's normal is nq + R np (the source normal moved)
+                const float4 np = __ldg(src_nrm + i);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    rn[r] = fmaf(h.Rh[3 * r], np.x, fmaf(h.Rh[3 * r + 1], np.y, h.Rh[3 * r + 2] * np.z));
+                nv.x += rn[0];
+                nv.y += rn[1];
+                nv.z += rn[2];
+            }
             const float hh = s * fmaf(dz, nv.z, fmaf(dy, nv.y, dx * nv.x));
             if (h.phase == PH_INIT) resid[i] = (double)fabsf(hh);
             const float g = h.welsch ? expf(-hh * hh * i2) : 1.0f;   // plain point-to-plane: weights 1
@@ -259,8 +271,11 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
 #pragma unroll
             for (int r = 0; r < 3; ++r)
                 y[r] = s * fmaf(h.Rh[3 * r], pt[0], fmaf(h.Rh[3 * r + 1], pt[1], h.Rh[3 * r + 2] * pt[2]));
-            const float z[6] = {y[1] * nv.z - y[2] * nv.y, y[2] * nv.x - y[0] * nv.z, y[0] * nv.y - y[1] * nv.x,
-                                nv.x, nv.y, nv.z};
+            // z = [y x n + (R np) x d; n] with d = s (x - q) (the second term: symmetric objective only)
+            const float d0 = s * dx, d1 = s * dy, d2 = s * dz;
+            const float z[6] = {y[1] * nv.z - y[2] * nv.y + (rn[1] * d2 - rn[2] * d1),
+                                y[2] * nv.x - y[0] * nv.z + (rn[2] * d0 - rn[0] * d2),
+                                y[0] * nv.y - y[1] * nv.x + (rn[0] * d1 - rn[1] * d0), nv.x, nv.y, nv.z};
             int t = 0;
 #pragma unroll
             for (int r = 0; r < 6; ++r) {
@@ -303,15 +318,33 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
         acc[16] = psi;
     } else {
         const float4 nv = __ldg(ix.nrm + j);
-        const double n0 = nv.x, n1 = nv.y, n2 = nv.z;
+        double n0 = nv.x, n1 = nv.y, n2 = nv.z;
+        const bool sym = src_nrm != nullptr && fricp::variant_sym(h.variant);
+        double rn[3] = {0.0, 0.0, 0.0};
+        if (sym) {   // symmetric objective: the pair's normal is nq + R np (the source normal moved)
+            const float4 np = __ldg(src_nrm + i);
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                rn[r] = h.R[3 * r] * (double)np.x + h.R[3 * r + 1] * (double)np.y + h.R[3 * r + 2] * (double)np.z;
+            n0 += rn[0];
+            n1 += rn[1];
+            n2 += rn[2];
+        }
         const double hh = s * (dx * n0 + dy * n1 + dz * n2);
         if (h.phase == PH_INIT) resid[i] = fabs(hh);
         const double g = h.welsch ? exp(-hh * hh * h.inv2nu2) : 1.0;   // plain point-to-plane: weights 1
-        // y = R p~ in normalised units; z = [y x n; n]
+        // y = R p~ in normalised units; z = [y x n; n], plus (R np) x d in the rotational part for the
+        // symmetric objective (d = s (x - q), the residual vector in normalised units)
         double y[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) y[r] = s * (h.R[3 * r] * pt[0] + h.R[3 * r + 1] * pt[1] + h.R[3 * r + 2] * pt[2]);
-        const double z[6] = {y[1] * n2 - y[2] * n1, y[2] * n0 - y[0] * n2, y[0] * n1 - y[1] * n0, n0, n1, n2};
+        double z[6] = {y[1] * n2 - y[2] * n1, y[2] * n0 - y[0] * n2, y[0] * n1 - y[1] * n0, n0, n1, n2};
+        if (sym) {
+            const double d0 = s * dx, d1 = s * dy, d2 = s * dz;
+            z[0] += rn[1] * d2 - rn[2] * d1;
+            z[1] += rn[2] * d0 - rn[0] * d2;
+            z[2] += rn[0] * d1 - rn[1] * d0;
+        }
         int t = 0;
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
@@ -330,13 +363,13 @@ __device__ __forceinline__ void accum_point(const StepHead &h, const Index &ix, 
 template <int VAR, int PREC>
 __device__ __forceinline__ bool accum_tile(const StepHead &h, PairState *st, const Index &ix, const float4 *src,
                                            const int *prev, double *resid, double *partial, int tile, int ntiles,
-                                           double *red, int *s_last) {
+                                           double *red, int *s_last, const float4 *src_nrm = nullptr) {
     constexpr int K = VAR ? kSumsP2PL : kSumsP2P;
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
     const int i = tile * kBlock + threadIdx.x;
-    if (i < h.M) accum_point<VAR, PREC>(h, ix, src, prev, resid, i, acc);
+    if (i < h.M) accum_point<VAR, PREC>(h, ix, src, prev, resid, i, acc, src_nrm);
     block_reduce_store<K>(acc, partial + (size_t)tile * K, red);
     __threadfence();
     __syncthreads();
