@@ -503,11 +503,51 @@ def precision_summary(fr, pair, dev, flush, steps=3, warmup=1):
             "oracle_result": "tests/golden/fullsize_config3_p2pl_welsch.json" if gold else None}
 
 
+def symmetric_summary(fr, pair, dev, flush, steps=3, warmup=1):
+    """Workload 3 under the Welsch-robust symmetric objective (source normals on
+    the device) beside the point-to-plane Alg. 2 it extends: time per whole
+    registration and the Eq. (13) RMSE against the ground-truth motion."""
+    import torch
+    Qd, Nd, Pd = dev
+    Sd = torch.from_numpy(pair.src_normals).cuda()
+    out = {}
+    for variant in ("p2pl_welsch", "sym_welsch"):
+        prm = fr.params_default(variant)
+
+        def run():
+            t = fr.target_create(Qd, Nd)
+            if variant == "sym_welsch":
+                r = fr.register_symmetric(t, Pd, Sd, params=prm)
+            else:
+                r = fr.register(t, Pd, params=prm)
+            return t, r
+        for _ in range(warmup):
+            run()[0].destroy()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record()
+            t, r = run()
+            ev1.record()
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            t.destroy()
+        ms = statistics.mean(times)
+        out[variant] = {"ms_per_registration": ms, "iterations": r["iterations"], "corr_passes": r["corr_passes"],
+                        "device_steps": r["device_steps"], "line_search_trials": r["line_search_trials"],
+                        "queries_per_s": pair.M * r["iterations"] / (ms / 1e3),
+                        "rmse_over_diag": rmse_of(pair.P, r["R"], r["t"], pair.R_gt, pair.t_gt) / pair.diag}
+    return {"workload": WORKLOAD, "steps": steps, "objectives": out}
+
+
 def nested_workloads(fr, data, flush, pair, dev, rt):
     t0 = time.perf_counter()
     out = {"single_torus_p2p": single_summary(fr, 1, "p2p", dict(max_iters=100), flush, steps=10, warmup=3),
            "single_height_field": single_summary(fr, 2, "p2p_welsch", {}, flush)}
     out["precision"] = precision_summary(fr, pair, dev, flush)
+    out["symmetric"] = symmetric_summary(fr, pair, dev, flush)
     out["batched"] = batched_summary(fr, data["batch"], steps=1, warmup=1)
     out["served"] = served_summary(fr, data["serve"], NESTED_SERVE_RATES, NESTED_SERVE_SECONDS)
     out["seconds"] = {"generation": data["gen_s"], "measurement": time.perf_counter() - t0}

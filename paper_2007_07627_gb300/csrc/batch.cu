@@ -796,11 +796,11 @@ struct fricp_server {
 
 namespace {
 
-// Device bytes of a target's index: points, normals, box tree and (once built)
+// Device bytes of a target's index: points, normals, box tree, oriented bucket boxes and (once built)
 // the FP16 storage.
 size_t target_bytes(const fricp_target *t) {
     const TargetDev &d = *fricp::target_dev(t);
-    size_t b = sizeof(float4) * (size_t)d.n * (d.has_normals ? 2 : 1) + sizeof(float4) * 4 * (size_t)d.L;
+    size_t b = sizeof(float4) * (size_t)d.n * (d.has_normals ? 2 : 1) + sizeof(float4) * 8 * (size_t)d.L;
     if (d.pts16) b += sizeof(ushort4) * (size_t)d.n;
     return b;
 }

@@ -8,6 +8,10 @@
 //                        nodes[2i] (lo) and nodes[2i+1] (hi), so the two children of
 //                        node i sit in one aligned 64-byte line nodes[4i .. 4i+3].
 //                        Leaf l is node L + l; empty buckets have an inverted box.
+//   obb   float4[4L]     oriented box of every bucket (same allocation, after the
+//                        nodes): centre c and half-extents h along three orthonormal
+//                        axes a_k fitted to the bucket's points, as
+//                        (c, h0) (a0, h1) (a1, h2) (a2, r), r the bucket's radius
 //   src   float4[M]      source points in Morton order, .w = original index bits
 //   PairState            one registration's solver state (FP64), ~2 KB
 //   partial double[T][K] per-tile reduction records (T = ceil(M / kBlock) tiles)
@@ -67,6 +71,7 @@ struct Index {
     const ushort4 *pts16;   // FP16 storage (x, y, z as half offsets in the bucket box), or null
     int n;
     int L;
+    const float4 *obb;      // oriented bucket boxes (4 float4 per bucket), or null: axis-aligned boxes only
 };
 
 enum Phase : int {
@@ -238,6 +243,27 @@ __device__ __forceinline__ float box_d2(float4 lo, float4 hi, const float xh[3],
     return fmaf(c, c, fmaf(b, b, a * a));
 }
 
+// Squared distance from x = xh + xl to a bucket's oriented box, in float. The
+// box is built (k_leaf_obb) from the exact float axes it stores, with half-
+// extents widened by 1e-6 relative plus 2e-6 of the bucket's radius; against
+// that widening, the float rounding of u = A ((xh - c) + xl) (at most ~5.2e-7 of
+// |x - c| per axis) leaves the result at most (1 + 8e-6) times the squared
+// distance to the bucket's nearest point. A bucket is skipped only when this
+// distance, shrunk by kObbShrink, still exceeds the bound: it can never hold a
+// point inside the tie window.
+constexpr float kObbShrink = 1.0f - 2e-5f;
+
+__device__ __forceinline__ float obb_d2(const float4 *o, const float xh[3], const float xl[3]) {
+    const float4 c = __ldg(o), a0 = __ldg(o + 1), a1 = __ldg(o + 2), a2 = __ldg(o + 3);
+    const float dx = (xh[0] - c.x) + xl[0];
+    const float dy = (xh[1] - c.y) + xl[1];
+    const float dz = (xh[2] - c.z) + xl[2];
+    const float e0 = fmaxf(fabsf(fmaf(a0.z, dz, fmaf(a0.y, dy, a0.x * dx))) - c.w, 0.0f);
+    const float e1 = fmaxf(fabsf(fmaf(a1.z, dz, fmaf(a1.y, dy, a1.x * dx))) - a0.w, 0.0f);
+    const float e2 = fmaxf(fabsf(fmaf(a2.z, dz, fmaf(a2.y, dy, a2.x * dx))) - a1.w, 0.0f);
+    return fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
+}
+
 __device__ __forceinline__ float cand_d2f(const NNLane &q, float4 p) {
     const float dx = (q.xh[0] - p.x) + q.xl[0];
     const float dy = (q.xh[1] - p.y) + q.xl[1];
@@ -334,6 +360,15 @@ __device__ __forceinline__ bool nn_offer(NNLane &q, float4 p, int j) {
     return false;
 }
 
+// Whether leaf node `leaf` (L + bucket) may hold a point within the lane's
+// bound by its oriented box (its axis-aligned box passed already). FP16
+// storage decodes points inside the axis-aligned box only, so it skips this test.
+template <int PREC = PREC_FP64>
+__device__ __forceinline__ bool obb_meets(const Index &ix, const NNLane &q, int leaf) {
+    if (PREC == PREC_FP16 || ix.obb == nullptr) return true;
+    return obb_d2(ix.obb + 4 * (leaf - ix.L), q.xh, q.xl) * kObbShrink <= q.bestf;
+}
+
 // Depth-first search from the root with the lane's current bound (q.bestf).
 // A lane whose bound starts finite (warm start, or a radius cap) only visits
 // buckets within that bound; if none holds a closer point the starting
@@ -386,7 +421,7 @@ __device__ __forceinline__ void nn_thread(const Index &ix, NNLane &q, int start_
                 node = c0;
                 continue;
             }
-        } else {
+        } else if (obb_meets(ix, q, node)) {
             const int beg = (node - ix.L) * kLeaf;
             const int end = min(beg + kLeaf, ix.n);
             for (int j = beg; j < end; ++j) nn_offer(q, __ldg(ix.pts + j), j);
@@ -515,7 +550,8 @@ __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, in
                 }
             } else {
                 leaf_ok = box_d2(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), q.xh, q.xl) * kShrink
-                          <= q.bestf;
+                              <= q.bestf &&
+                          obb_meets<PREC>(ix, q, node);
             }
         }
         int base = sp;
@@ -655,7 +691,8 @@ __device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk
                 }
             } else {
                 leaf_ok = box_d2(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), q.xh, q.xl) * kShrink
-                          <= q.bestf;
+                              <= q.bestf &&
+                          obb_meets<PREC>(ix, q, node);
             }
         }
         int base = sp;
@@ -703,7 +740,9 @@ __device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk
 //     round: sub-lane u tests the children of nodes u, u + 4, ... of the round
 //     against its own query's ball with the pruning test of the serial search,
 //     and a node is kept when it is within some query's bound;
-//   - the buckets kept are staged, two per pass, in shared memory (one
+//   - the buckets kept wait in a list; before it is scanned, buckets whose
+//     oriented box lies beyond every query's current bound are dropped;
+//   - the buckets left are staged, two per pass, in shared memory (one
 //     coalesced 16-byte load per lane; FP16 storage is decoded here, once per
 //     point); sub-lane u offers staged points u, u + 4, ..., u + 28 to its
 //     query, and the group shares its float bound after every pass.
@@ -819,6 +858,35 @@ __device__ __forceinline__ void tile_scan(const Index &ix, NNLane &q, bool easy,
     __syncwarp();
 }
 
+// Drop from pend[0 .. np) the buckets whose oriented box is beyond every
+// query's bound (sub-lane u tests buckets u, u + 4, ... for its group's
+// query); returns how many are left, in their order. A bucket some query may
+// need passes that query's test, so nothing it needs is dropped.
+template <int PREC>
+__device__ __forceinline__ int tile_obb_filter(const Index &ix, const NNLane &q, bool easy, int *pend, int np) {
+    if (PREC == PREC_FP16 || ix.obb == nullptr) return np;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int u = lane & 3;
+    int out = 0;
+    for (int k0 = 0; k0 < np; k0 += 4) {
+        const int k = k0 + u;
+        const int leaf = k < np ? pend[k] : 0;
+        const bool pass = k < np && easy && obb_d2(ix.obb + 4 * (leaf - ix.L), q.xh, q.xl) * kObbShrink <= q.bestf;
+        unsigned m = __ballot_sync(FULL, pass);
+        m |= m >> 16;
+        m |= m >> 8;
+        m |= m >> 4;   // bit b: some group keeps bucket k0 + b
+        __syncwarp();
+        if (lane == 0)   // in place, in order: each write lands at or before the slot it copies
+            for (int b = 0; b < 4; ++b)
+                if ((m >> b) & 1u) pend[out++] = pend[k0 + b];
+        out = __shfl_sync(FULL, out, 0);
+        __syncwarp();
+    }
+    return out;
+}
+
 // Append the nodes of `cand` (lanes t < nc hold one each) whose bit is set in
 // `keep`: buckets to pend, inner nodes to the stack. Returns false when either
 // would overflow.
@@ -881,6 +949,7 @@ __device__ __forceinline__ unsigned tile_nn(const Index &ix, NNLane &q, bool liv
     }
     while (ok && (sp > 0 || np > 0)) {
         if (np >= kTileDrain || (sp == 0 && np > 0)) {
+            np = tile_obb_filter<PREC>(ix, q, easy, pend, np);
             tile_scan<PREC>(ix, q, easy, pend, np, stage);
             np = 0;
         }
@@ -945,7 +1014,8 @@ struct TargetDev {
     int has_normals;
     float4 *pts;
     float4 *nrm;
-    float4 *nodes;
+    float4 *nodes;    // 4L float4 of boxes, then 4L float4 of oriented bucket boxes (one allocation)
+    float4 *obb;      // = nodes + 4L
     ushort4 *pts16;   // FP16 storage, built on first use (build_fp16_storage)
     double centroid[3];
     float lo[3], hi[3];
@@ -954,7 +1024,7 @@ struct TargetDev {
     double E_Q, H_Q;
 };
 
-inline Index make_index(const TargetDev &t) { return Index{t.pts, t.nrm, t.nodes, t.pts16, (int)t.n, t.L}; }
+inline Index make_index(const TargetDev &t) { return Index{t.pts, t.nrm, t.nodes, t.pts16, (int)t.n, t.L, t.obb}; }
 
 // Per-thread accounting behind fricp_counters (defined in api.cu).
 struct Counters {
