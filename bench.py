@@ -27,6 +27,10 @@ their summaries in the same JSON line ("workloads"; --no-nested skips them):
                          the FP64 reference mode, each with its error against
                          the FP64 oracle's result (tests/golden, written by the
                          oracle alone);
+  symmetric              workload 3 under the Welsch-robust symmetric objective
+                         (Sec. 7's proposed extension, with the source's normals)
+                         beside point-to-plane: time and Eq. (13) RMSE to the
+                         ground-truth motion;
   batched                workload 4: 256 pairs (M, N log-uniform in [2k, 200k],
                          variants in equal thirds) in one fricp_batch_register
                          vs the plain path one pair at a time;

@@ -165,7 +165,8 @@ fricp_status fricp_params_default(int32_t variant, fricp_params *out);
 /* Build the target set Q once (Sec. 3: Q is fixed over all iterations): copies
  * q_xyz (and q_normals if not NULL; they must be unit length within 1e-3) to
  * the device, builds the exact nearest-neighbour index (Morton-ordered buckets
- * under a complete bounding-box tree) and the centroid used by the
+ * under a complete bounding-box tree, each bucket also bounded by an oriented
+ * box along its points' principal axes) and the centroid used by the
  * normalisation. n >= 1. The handle owns all its device memory until
  * fricp_target_destroy. Errors: EINVAL (bad pointer/size/NaN/non-unit normal),
  * ENOMEM, ECUDA. */
@@ -315,8 +316,9 @@ typedef struct fricp_server fricp_server;
 /* hbm_budget: bytes of device memory the requests in flight may hold (0 = half
  * of the free device memory): a request's own buffers (28 B per source point,
  * 224 B per 256 points and one solver state of a few KB) and the index of its
- * target (16 B per point, 16 more with normals, 64 B per bucket of 16, 8 B per
- * point of FP16 storage), a target counted once however many requests in
+ * target (16 B per point, 16 more with normals, 128 B per bucket of 16 for its
+ * axis-aligned and oriented boxes, 8 B per point of FP16 storage), a target
+ * counted once however many requests in
  * flight share it. Requests are admitted in FIFO order while a slot is free
  * and the budget holds them. max_slots: requests in flight at most
  * (1..4096). steps_per_sync: device steps per graph replay. max_queue:
@@ -401,8 +403,10 @@ fricp_status fricp_eval_pass(const fricp_target *target, const float *p_xyz, int
  *     library keeps until the process exits. The call makes no cudaMalloc,
  *     cudaFree or other allocating call.
  * The first call on a device looks up the array's device address (set-up, once
- * per device, with that device current); make that first call before any
- * stream capture. All calls share the one array and it keeps the last call's
+ * per device, with that device current; the cached address does not survive
+ * cudaDeviceReset). Every call copies its inputs from host memory and waits for
+ * its stream, so no call can be captured into a CUDA graph. All calls share
+ * the one array and it keeps the last call's
  * contents; each call rewrites everything it reads, but calls that overlap on
  * the GPU (different streams or threads) race on it: issue them one after
  * another. Blocks until `out` is filled. Errors: EINVAL, EUNSUPPORTED,

@@ -477,6 +477,37 @@ __device__ bool warp_knn6(const Index &ix, int i, const float xq[3], Best6 &b, i
 
 constexpr int kKnnBlock = 128;
 
+// Per-point statistics of point i from its six nearest (Sec. 4.3, Sec. 5): the
+// median of the six distances and, with normals, of the six distances to the
+// point's tangent plane (the median of six: the mean of the 3rd and 4th).
+__device__ void write_knn6_stats(const Index &ix, int i, const float xq[3], const Best6 &b, double *stat_d,
+                                 double *stat_h) {
+    const double x0 = xq[0], x1 = xq[1], x2 = xq[2];
+    stat_d[i] = 0.5 * (sqrt(b.d[2]) + sqrt(b.d[3]));
+    if (stat_h != nullptr) {
+        const float4 ni = ix.nrm[i];
+        double h[6];
+        for (int s = 0; s < 6; ++s) {
+            if (b.j[s] < 0) {
+                h[s] = INFINITY;
+                continue;
+            }
+            const float4 q = ix.pts[b.j[s]];
+            h[s] = fabs(((double)q.x - x0) * ni.x + ((double)q.y - x1) * ni.y + ((double)q.z - x2) * ni.z);
+        }
+        for (int a = 1; a < 6; ++a) {   // insertion sort of six values
+            const double v = h[a];
+            int c = a - 1;
+            while (c >= 0 && h[c] > v) {
+                h[c + 1] = h[c];
+                --c;
+            }
+            h[c + 1] = v;
+        }
+        stat_h[i] = 0.5 * (h[2] + h[3]);
+    }
+}
+
 __global__ void __launch_bounds__(kKnnBlock) k_knn6_stats(Index ix, double *__restrict__ stat_d,
                                                           double *__restrict__ stat_h, int *__restrict__ overflow) {
     __shared__ int s_stk[kKnnBlock / 32][kWarpStack];
@@ -490,30 +521,179 @@ __global__ void __launch_bounds__(kKnnBlock) k_knn6_stats(Index ix, double *__re
             if (lane == 0) *overflow = 1;
             continue;
         }
-        if (lane != 0) continue;
-        const double x0 = xq[0], x1 = xq[1], x2 = xq[2];
-        stat_d[i] = 0.5 * (sqrt(b.d[2]) + sqrt(b.d[3]));
-        if (stat_h != nullptr) {
-            const float4 ni = ix.nrm[i];
-            double h[6];
-            for (int s = 0; s < 6; ++s) {
-                if (b.j[s] < 0) {
-                    h[s] = INFINITY;
-                    continue;
+        if (lane == 0) write_knn6_stats(ix, i, xq, b, stat_d, stat_h);
+    }
+}
+
+// Six-neighbour statistics by tiles: a warp takes the 32 Morton-consecutive
+// target points of buckets 2g and 2g + 1, one per lane, each lane keeping its
+// own six nearest (Best6, the same (FP64 distance, index) order and float
+// pre-test as warp_knn6).
+//   1. Each lane offers the tile's other 31 points to its six: its sixth
+//      distance is then an upper bound of its true sixth distance, and R, the
+//      largest over the lanes (rounded up to float), bounds them all.
+//   2. Every point within sqrt(R) of some lane's point lies within sqrt(R) of
+//      the two buckets' common box (the tree node above them), so the buckets
+//      whose box is within that distance of that box (walk from the node's path
+//      siblings, box-to-box distance, kShrink slack) hold every candidate.
+//   3. Each lane offers the points of those buckets to its six, pruning with
+//      its own sixth distance.
+// The six selected are therefore the exact six of warp_knn6. A tile whose
+// bucket list does not fit (a scattered tile, or fewer than seven points in
+// it) is searched point by point with warp_knn6 instead.
+constexpr int kKnnCand = 192;   // candidate buckets per tile
+
+__device__ __forceinline__ float box_box_d2(float4 alo, float4 ahi, float4 blo, float4 bhi) {
+    const float gx = fmaxf(fmaxf(alo.x - bhi.x, blo.x - ahi.x), 0.0f);
+    const float gy = fmaxf(fmaxf(alo.y - bhi.y, blo.y - ahi.y), 0.0f);
+    const float gz = fmaxf(fmaxf(alo.z - bhi.z, blo.z - ahi.z), 0.0f);
+    return fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+}
+
+__device__ __forceinline__ void knn6_offer_own(Best6 &b, float4 q, const float xq[3], int j) {
+    const float fx = q.x - xq[0], fy = q.y - xq[1], fz = q.z - xq[2];
+    if (fmaf(fz, fz, fmaf(fy, fy, fx * fx)) * kShrink <= b.bound) {
+        const double a0 = (double)q.x - (double)xq[0], a1 = (double)q.y - (double)xq[1],
+                     a2 = (double)q.z - (double)xq[2];
+        best6_insert(b, a0 * a0 + a1 * a1 + a2 * a2, __float_as_int(q.w), j);
+    }
+}
+
+// Returns false when the candidate list or the walk's stack would overflow.
+__device__ bool tile_knn6(const Index &ix, int g, int i, bool live, const float xq[3], Best6 &b, int *stk,
+                          int *cand) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int s = 0; s < 6; ++s) {
+        b.d[s] = INFINITY;
+        b.o[s] = 0x7fffffff;
+        b.j[s] = -1;
+    }
+    b.bound = INFINITY;
+    const int i0 = 32 * g;
+    const float4 mine = live ? __ldg(ix.pts + i) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int t = 0; t < 32; ++t) {   // 1. the tile's own points
+        float4 q;
+        q.x = __shfl_sync(FULL, mine.x, t);
+        q.y = __shfl_sync(FULL, mine.y, t);
+        q.z = __shfl_sync(FULL, mine.z, t);
+        q.w = __shfl_sync(FULL, mine.w, t);
+        if (live && t != lane && i0 + t < ix.n) knn6_offer_own(b, q, xq, i0 + t);
+    }
+    float R = live ? b.bound : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(FULL, R, o));
+    if (!(R < INFINITY)) return false;
+    // 2. buckets within sqrt(R) of the tile's box (node P above buckets 2g, 2g + 1)
+    int depth = 0;
+    while ((1 << depth) < ix.L) ++depth;
+    const int P = (ix.L >> 1) + g;
+    const float4 glo = __ldg(ix.nodes + 2 * P), ghi = __ldg(ix.nodes + 2 * P + 1);
+    int sp = 0, nc = 0;
+    {
+        int c = 0;
+        bool pass = false;
+        if (lane < depth - 1) {   // siblings of P's path, from the root's children down
+            c = (P >> (depth - 2 - lane)) ^ 1;
+            pass = box_box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), glo, ghi) * kShrink <= R;
+        }
+        const unsigned m = __ballot_sync(FULL, pass);
+        if (pass) stk[__popc(m & below)] = c;
+        sp = __popc(m);
+    }
+    __syncwarp();
+    while (sp > 0) {
+        const int k = min(32, sp);
+        const int node = (lane < k) ? stk[sp - 1 - lane] : 0;
+        sp -= k;
+        __syncwarp();
+        int c[4] = {0, 0, 0, 0};
+        bool ok[4] = {false, false, false, false};
+        bool leaf = false;
+        if (node != 0) {
+            if (node < ix.L) {
+                const int level = 31 - __clz(node);
+                if (level < depth - 1) {
+                    const float4 *bx = ix.nodes + 8 * node;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        c[q] = 4 * node + q;
+                        ok[q] = box_box_d2(__ldg(bx + 2 * q), __ldg(bx + 2 * q + 1), glo, ghi) * kShrink <= R;
+                    }
+                } else {
+                    const float4 *bx = ix.nodes + 4 * node;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        c[q] = 2 * node + q;
+                        ok[q] = box_box_d2(__ldg(bx + 2 * q), __ldg(bx + 2 * q + 1), glo, ghi) * kShrink <= R;
+                    }
                 }
-                const float4 q = ix.pts[b.j[s]];
-                h[s] = fabs(((double)q.x - x0) * ni.x + ((double)q.y - x1) * ni.y + ((double)q.z - x2) * ni.z);
+            } else {
+                leaf = true;   // tested when it was pushed
             }
-            for (int a = 1; a < 6; ++a) {   // insertion sort of six values
-                const double v = h[a];
-                int c = a - 1;
-                while (c >= 0 && h[c] > v) {
-                    h[c + 1] = h[c];
-                    --c;
-                }
-                h[c + 1] = v;
+        }
+        const unsigned lm = __ballot_sync(FULL, leaf);
+        if (nc + __popc(lm) > kKnnCand) return false;
+        if (leaf) cand[nc + __popc(lm & below)] = node;
+        nc += __popc(lm);
+        int base = sp;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const unsigned mq = __ballot_sync(FULL, ok[q]);
+            if (base + __popc(mq) > kWarpStack - kKnnCand) return false;
+            if (ok[q]) stk[base + __popc(mq & below)] = c[q];
+            base += __popc(mq);
+        }
+        sp = base;
+        __syncwarp();
+    }
+    // 3. every lane offers the candidates' points to its own six
+    for (int k = 0; k < nc; ++k) {
+        const int beg = (cand[k] - ix.L) * kLeaf;
+        const int end = min(beg + kLeaf, ix.n);
+        if (live)
+            for (int j = beg; j < end; ++j) knn6_offer_own(b, __ldg(ix.pts + j), xq, j);
+    }
+    __syncwarp();
+    return true;
+}
+
+__global__ void __launch_bounds__(kKnnBlock) k_knn6_tile(Index ix, double *__restrict__ stat_d,
+                                                         double *__restrict__ stat_h, int *__restrict__ overflow) {
+    __shared__ int s_stk[kKnnBlock / 32][kWarpStack];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int wpb = kKnnBlock / 32;
+    const int ngroups = (ix.n + 31) / 32;
+    int *stk = s_stk[w];
+    int *cand = s_stk[w] + (kWarpStack - kKnnCand);
+    for (int g = blockIdx.x * wpb + w; g < ngroups; g += gridDim.x * wpb) {
+        const int i = 32 * g + lane;
+        const bool live = i < ix.n;
+        float xq[3] = {0.0f, 0.0f, 0.0f};
+        if (live) {
+            const float4 qi = __ldg(ix.pts + i);
+            xq[0] = qi.x;
+            xq[1] = qi.y;
+            xq[2] = qi.z;
+        }
+        Best6 b;
+        if (tile_knn6(ix, g, i, live, xq, b, stk, cand)) {
+            if (live) write_knn6_stats(ix, i, xq, b, stat_d, stat_h);
+            continue;
+        }
+        __syncwarp();
+        for (int t = 0; t < 32 && 32 * g + t < ix.n; ++t) {   // point by point
+            const int it = 32 * g + t;
+            const float4 qt = __ldg(ix.pts + it);
+            const float xt[3] = {qt.x, qt.y, qt.z};
+            Best6 bt;
+            if (!warp_knn6(ix, it, xt, bt, stk)) {
+                if (lane == 0) *overflow = 1;
+                continue;
             }
-            stat_h[i] = 0.5 * (h[2] + h[3]);
+            if (lane == 0) write_knn6_stats(ix, it, xt, bt, stat_d, stat_h);
+            __syncwarp();
         }
     }
 }
@@ -1067,7 +1247,14 @@ cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t blocks = std::min<int64_t>((t->n + kKnnBlock / 32 - 1) / (kKnnBlock / 32),
                                                  (int64_t)(sms > 0 ? sms : 152) * 16);
-        k_knn6_stats<<<(unsigned)blocks, kKnnBlock, 0, s>>>(ix, sd, sh, flag);
+        if (t->L >= 4) {
+            const int64_t tiles = (t->n + 31) / 32;
+            const int64_t tblocks = std::min<int64_t>((tiles + kKnnBlock / 32 - 1) / (kKnnBlock / 32),
+                                                      (int64_t)(sms > 0 ? sms : 152) * 16);
+            k_knn6_tile<<<(unsigned)tblocks, kKnnBlock, 0, s>>>(ix, sd, sh, flag);
+        } else {
+            k_knn6_stats<<<(unsigned)blocks, kKnnBlock, 0, s>>>(ix, sd, sh, flag);
+        }
         counters().launches += 1;
         const unsigned mblocks = (unsigned)std::min<int64_t>((t->n + 255) / 256, (int64_t)(sms > 0 ? sms : 152) * 4);
         for (int which = 0; which < (sh ? 2 : 1); ++which) {
