@@ -186,6 +186,7 @@ constexpr float kTieWindow = 1.0f + 2e-6f;
 
 struct NNLane {
     float xh[3], xl[3];
+    float xdn[3], xup[3];    // xh + xl rounded down and up: float bounds of x for the box tests
     float bestf;             // float bound (smallest float distance seen)
     float best_hi, best_lo;  // double-float squared distance of the winner
     int best_j;
@@ -264,6 +265,17 @@ __device__ __forceinline__ float obb_d2(const float4 *o, const float xh[3], cons
     return fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
 }
 
+// Box test of a search lane: xdn <= x <= xup on every axis, so lo - xup and
+// xdn - hi never exceed the true gaps lo - x and x - hi (each subtraction then
+// rounds relative to its result, which kShrink covers): two operations per axis
+// fewer than box_d2 on the double-float pair.
+__device__ __forceinline__ float box_d2q(float4 lo, float4 hi, const NNLane &q) {
+    const float a = fmaxf(fmaxf(lo.x - q.xup[0], q.xdn[0] - hi.x), 0.0f);
+    const float b = fmaxf(fmaxf(lo.y - q.xup[1], q.xdn[1] - hi.y), 0.0f);
+    const float c = fmaxf(fmaxf(lo.z - q.xup[2], q.xdn[2] - hi.z), 0.0f);
+    return fmaf(c, c, fmaf(b, b, a * a));
+}
+
 __device__ __forceinline__ float cand_d2f(const NNLane &q, float4 p) {
     const float dx = (q.xh[0] - p.x) + q.xl[0];
     const float dy = (q.xh[1] - p.y) + q.xl[1];
@@ -296,6 +308,8 @@ __device__ __forceinline__ void nn_init(NNLane &q, const float xh[3], const floa
     for (int a = 0; a < 3; ++a) {
         q.xh[a] = xh[a];
         q.xl[a] = xl[a];
+        q.xdn[a] = __fadd_rd(xh[a], xl[a]);
+        q.xup[a] = __fadd_ru(xh[a], xl[a]);
     }
     q.bestf = __int_as_float(0x7f800000);
     q.best_hi = __int_as_float(0x7f800000);
@@ -392,7 +406,7 @@ __device__ __forceinline__ void nn_thread(const Index &ix, NNLane &q, int start_
         for (int a = ix.L + start_leaf; a > 1; a >>= 1) sib[ns++] = a ^ 1;
         for (int k = ns - 1; k >= 0; --k) {
             const int c = sib[k];
-            const float d = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q.xh, q.xl);
+            const float d = box_d2q(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q);
             if (d * kShrink <= q.bestf) {
                 stk[sp] = c;
                 stkd[sp] = d;
@@ -405,8 +419,8 @@ __device__ __forceinline__ void nn_thread(const Index &ix, NNLane &q, int start_
         if (node < ix.L) {
             const float4 *b = ix.nodes + 4 * node;
             const float4 lo0 = __ldg(b), hi0 = __ldg(b + 1), lo1 = __ldg(b + 2), hi1 = __ldg(b + 3);
-            float d0 = box_d2(lo0, hi0, q.xh, q.xl);
-            float d1 = box_d2(lo1, hi1, q.xh, q.xl);
+            float d0 = box_d2q(lo0, hi0, q);
+            float d1 = box_d2q(lo1, hi1, q);
             int c0 = 2 * node, c1 = c0 + 1;
             if (d1 < d0) {
                 const float td = d0; d0 = d1; d1 = td;
@@ -497,8 +511,8 @@ __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, in
         int node = 1;
         while (node < ix.L) {
             const float4 *b = ix.nodes + 4 * node;
-            const float d0 = box_d2(__ldg(b), __ldg(b + 1), q.xh, q.xl);
-            const float d1 = box_d2(__ldg(b + 2), __ldg(b + 3), q.xh, q.xl);
+            const float d0 = box_d2q(__ldg(b), __ldg(b + 1), q);
+            const float d1 = box_d2q(__ldg(b + 2), __ldg(b + 3), q);
             node = 2 * node + (d1 < d0 ? 1 : 0);
         }
         start_leaf = node - ix.L;
@@ -509,7 +523,7 @@ __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, in
         bool pass = false;
         if (lane < depth) {   // the sibling of the path node at level lane + 1
             c = ((ix.L + start_leaf) >> (depth - 1 - lane)) ^ 1;
-            pass = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q.xh, q.xl) * kShrink <= q.bestf;
+            pass = box_d2q(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q) * kShrink <= q.bestf;
         }
         const unsigned m = __ballot_sync(FULL, pass);
         if (pass) stk[__popc(m & below)] = c;
@@ -538,18 +552,18 @@ __device__ __forceinline__ bool warp_nn(const Index &ix, NNLane &q, int *stk, in
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         c[g] = 4 * node + g;
-                        ok[g] = box_d2(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q.xh, q.xl) * kShrink <= q.bestf;
+                        ok[g] = box_d2q(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q) * kShrink <= q.bestf;
                     }
                 } else {
                     const float4 *b = ix.nodes + 4 * node;
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {
                         c[g] = 2 * node + g;
-                        ok[g] = box_d2(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q.xh, q.xl) * kShrink <= q.bestf;
+                        ok[g] = box_d2q(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q) * kShrink <= q.bestf;
                     }
                 }
             } else {
-                leaf_ok = box_d2(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), q.xh, q.xl) * kShrink
+                leaf_ok = box_d2q(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), q) * kShrink
                               <= q.bestf &&
                           obb_meets<PREC>(ix, q, node);
             }
@@ -637,8 +651,8 @@ __device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk
         int node = 1;
         while (node < ix.L) {
             const float4 *b = ix.nodes + 4 * node;
-            const float d0 = box_d2(__ldg(b), __ldg(b + 1), q.xh, q.xl);
-            const float d1 = box_d2(__ldg(b + 2), __ldg(b + 3), q.xh, q.xl);
+            const float d0 = box_d2q(__ldg(b), __ldg(b + 1), q);
+            const float d1 = box_d2q(__ldg(b + 2), __ldg(b + 3), q);
             node = 2 * node + (d1 < d0 ? 1 : 0);
         }
         start_leaf = node - ix.L;
@@ -650,7 +664,7 @@ __device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk
         bool pass = false;
         if (live && lv < depth) {
             c = ((ix.L + start_leaf) >> (depth - 1 - lv)) ^ 1;
-            pass = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q.xh, q.xl) * kShrink <= q.bestf;
+            pass = box_d2q(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), q) * kShrink <= q.bestf;
         }
         const unsigned m = __ballot_sync(FULL, pass) & hmask;
         if (pass) stk[sp + __popc(m & below)] = c;
@@ -679,18 +693,18 @@ __device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         c[g] = 4 * node + g;
-                        ok[g] = box_d2(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q.xh, q.xl) * kShrink <= q.bestf;
+                        ok[g] = box_d2q(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q) * kShrink <= q.bestf;
                     }
                 } else {
                     const float4 *b = ix.nodes + 4 * node;
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {
                         c[g] = 2 * node + g;
-                        ok[g] = box_d2(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q.xh, q.xl) * kShrink <= q.bestf;
+                        ok[g] = box_d2q(__ldg(b + 2 * g), __ldg(b + 2 * g + 1), q) * kShrink <= q.bestf;
                     }
                 }
             } else {
-                leaf_ok = box_d2(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), q.xh, q.xl) * kShrink
+                leaf_ok = box_d2q(__ldg(ix.nodes + 2 * node), __ldg(ix.nodes + 2 * node + 1), q) * kShrink
                               <= q.bestf &&
                           obb_meets<PREC>(ix, q, node);
             }
@@ -790,7 +804,7 @@ __device__ __forceinline__ void group4_best(NNLane &q) {
 }
 
 __device__ __forceinline__ bool ball_meets(const NNLane &q, bool easy, float4 lo, float4 hi) {
-    return easy && box_d2(lo, hi, q.xh, q.xl) * kShrink <= q.bestf;
+    return easy && box_d2q(lo, hi, q) * kShrink <= q.bestf;
 }
 
 // Asynchronous 16-byte global -> shared copies (cp.async, cached in L1).
