@@ -754,9 +754,7 @@ __device__ __forceinline__ bool halfwarp_nn(const Index &ix, NNLane &q, int *stk
 //     round: sub-lane u tests the children of nodes u, u + 4, ... of the round
 //     against its own query's ball with the pruning test of the serial search,
 //     and a node is kept when it is within some query's bound;
-//   - the buckets kept wait in a list; before it is scanned, buckets whose
-//     oriented box lies beyond every query's current bound are dropped;
-//   - the buckets left are staged, two per pass, in shared memory (one
+//   - the buckets kept are staged, two per pass, in shared memory (one
 //     coalesced 16-byte load per lane; FP16 storage is decoded here, once per
 //     point); sub-lane u offers staged points u, u + 4, ..., u + 28 to its
 //     query, and the group shares its float bound after every pass.
@@ -872,35 +870,6 @@ __device__ __forceinline__ void tile_scan(const Index &ix, NNLane &q, bool easy,
     __syncwarp();
 }
 
-// Drop from pend[0 .. np) the buckets whose oriented box is beyond every
-// query's bound (sub-lane u tests buckets u, u + 4, ... for its group's
-// query); returns how many are left, in their order. A bucket some query may
-// need passes that query's test, so nothing it needs is dropped.
-template <int PREC>
-__device__ __forceinline__ int tile_obb_filter(const Index &ix, const NNLane &q, bool easy, int *pend, int np) {
-    if (PREC == PREC_FP16 || ix.obb == nullptr) return np;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int u = lane & 3;
-    int out = 0;
-    for (int k0 = 0; k0 < np; k0 += 4) {
-        const int k = k0 + u;
-        const int leaf = k < np ? pend[k] : 0;
-        const bool pass = k < np && easy && obb_d2(ix.obb + 4 * (leaf - ix.L), q.xh, q.xl) * kObbShrink <= q.bestf;
-        unsigned m = __ballot_sync(FULL, pass);
-        m |= m >> 16;
-        m |= m >> 8;
-        m |= m >> 4;   // bit b: some group keeps bucket k0 + b
-        __syncwarp();
-        if (lane == 0)   // in place, in order: each write lands at or before the slot it copies
-            for (int b = 0; b < 4; ++b)
-                if ((m >> b) & 1u) pend[out++] = pend[k0 + b];
-        out = __shfl_sync(FULL, out, 0);
-        __syncwarp();
-    }
-    return out;
-}
-
 // Append the nodes of `cand` (lanes t < nc hold one each) whose bit is set in
 // `keep`: buckets to pend, inner nodes to the stack. Returns false when either
 // would overflow.
@@ -963,7 +932,6 @@ __device__ __forceinline__ unsigned tile_nn(const Index &ix, NNLane &q, bool liv
     }
     while (ok && (sp > 0 || np > 0)) {
         if (np >= kTileDrain || (sp == 0 && np > 0)) {
-            np = tile_obb_filter<PREC>(ix, q, easy, pend, np);
             tile_scan<PREC>(ix, q, easy, pend, np, stage);
             np = 0;
         }
