@@ -33,8 +33,13 @@ thread_local std::string g_err;
 
 // Run fused steps until the state machine is done. Returns the status and the
 // summed device time of the step launches when timing is requested.
+// init_m > 0: the state starts at an initial pass flagged init_median_ext; it
+// runs first, on its own, and its nu_max median over the init_m residuals is
+// selected by the whole GPU (launch_median) before the first stage starts
+// (launch_after_init) -- the same median the one-block select in the step would
+// find.
 fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const fricp_params &prm, cudaStream_t s,
-                       PairState *st_dev, bool *leak, double *pass_ms, double *search_ms) {
+                       PairState *st_dev, bool *leak, double *pass_ms, double *search_ms, int64_t init_m = 0) {
     using clock = std::chrono::steady_clock;
     const int prec = prm.precision;
     const auto deadline = clock::now() + std::chrono::duration_cast<clock::duration>(
@@ -68,6 +73,34 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
     int64_t steps = 0;
     *pass_ms = 0.0;
     *search_ms = 0.0;
+    DevBuf<double> mscr;
+    if (rs == FRICP_OK && init_m > 0) {
+        const size_t words = fricp::kMedianScratchBytes / sizeof(double);
+        if (mscr.alloc(words + 1, s) != cudaSuccess) {
+            rs = fail(FRICP_ENOMEM, "device allocation for the median select");
+        } else {
+            double *med = mscr.p + words;
+            cudaEvent_t iev[3] = {nullptr, nullptr, nullptr};
+            if (timing)
+                for (auto &ev : iev) cudaEventCreate(&ev);
+            if (timing) cudaEventRecord(iev[0], s);
+            e = fricp::launch_step(a, variant, prec, ntiles, s, timing ? iev[1] : nullptr, prm.search);
+            if (timing) cudaEventRecord(iev[2], s);
+            if (e == cudaSuccess) e = fricp::launch_median(a.resid, (int)init_m, mscr.p, med, s);
+            if (e == cudaSuccess) e = fricp::launch_after_init(a.st, med, s);
+            if (e != cudaSuccess) rs = cuda_fail(e, "launching the initial pass");
+            steps = 1;
+            if (timing && rs == FRICP_OK && cudaEventSynchronize(iev[2]) == cudaSuccess) {
+                float ms = 0.0f, ms_nn = 0.0f;
+                cudaEventElapsedTime(&ms, iev[0], iev[2]);
+                cudaEventElapsedTime(&ms_nn, iev[0], iev[1]);
+                *pass_ms += ms;
+                *search_ms += ms_nn;
+            }
+            if (timing)
+                for (auto &ev : iev) cudaEventDestroy(ev);
+        }
+    }
     while (rs == FRICP_OK) {
         if (use_graph) {
             e = cudaGraphLaunch(graph.exec, s);
@@ -113,6 +146,7 @@ fricp_status run_steps(const fricp::StepArgs &a, int variant, int ntiles, const 
     }
     for (auto &ev : tev) cudaEventDestroy(ev);
     cudaEventDestroy(poll);
+    mscr.leak = *leak;
     return rs;
 }
 
@@ -344,6 +378,7 @@ fricp_status register_impl(const fricp_target *t, const float *p_xyz, const floa
         h.rec = rec.p;
         h.rec_cap = steps_capacity;
     }
+    h.init_median_ext = h.phase == fricp::PH_INIT ? 1 : 0;
     e = cudaMemcpyAsync(st_dev.p, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the solver state");
     counters().h2d += sizeof(h);
@@ -361,7 +396,7 @@ fricp_status register_impl(const fricp_target *t, const float *p_xyz, const floa
     a.trace = trace_capacity > 0 ? trace_dev.p : nullptr;
     bool leak = false;
     double pass_ms = 0.0, search_ms = 0.0;
-    st = run_steps(a, prm.variant, ntiles, prm, s, st_dev.p, &leak, &pass_ms, &search_ms);
+    st = run_steps(a, prm.variant, ntiles, prm, s, st_dev.p, &leak, &pass_ms, &search_ms, h.init_median_ext ? m : 0);
     if (leak) {
         src.leak = st_dev.leak = partial.leak = resid.leak = trace_dev.leak = prev.leak = rec.leak = src_nrm.leak = true;
         p.owned = nullptr;

@@ -116,6 +116,8 @@ struct PairState {
     int capexit;            // the running line search started from a cap check
     int ls_l;
     int hlen;
+    int init_median_ext;    // the first pass leaves the nu_max median to the host's grid-wide select (k_after_init)
+    int pad0;
     double nu;
     double E_prev;
     double tau;
@@ -1039,5 +1041,13 @@ cudaError_t launch_closest(const TargetDev *t, const float *p_dev, int64_t m, co
 cudaError_t launch_step(const StepArgs &a, int variant, int prec, int ntiles, cudaStream_t s,
                         cudaEvent_t mid = nullptr, int search = FRICP_SEARCH_QUERY);
 cudaError_t launch_setup_eval_xi(PairState *st, const double *T_normalized12, cudaStream_t s);
+// Median of n non-negative doubles (the mean of the two middle order
+// statistics, exact) by a grid-wide 8-bit radix select; `scratch` holds
+// kMedianScratchBytes of device memory, the result lands in *out_dev.
+constexpr int kMedianScratchBytes = 4096;
+cudaError_t launch_median(const double *v, int n, void *scratch, double *out_dev, cudaStream_t s);
+// After a first pass run with init_median_ext: nu_max from the median at
+// *median_dev and the first nu stage (start_after_init).
+cudaError_t launch_after_init(PairState *st, const double *median_dev, cudaStream_t s);
 
 }  // namespace fricp

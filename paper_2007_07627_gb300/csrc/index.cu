@@ -1225,6 +1225,22 @@ cudaError_t build_fp16_storage(TargetDev *t, cudaStream_t s) {
     return cudaSuccess;
 }
 
+cudaError_t launch_median(const double *v, int n, void *scratch, double *out_dev, cudaStream_t s) {
+    static_assert(sizeof(MedianState) <= (size_t)kMedianScratchBytes, "median scratch");
+    MedianState *mst = static_cast<MedianState *>(scratch);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned mblocks = (unsigned)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)(sms > 0 ? sms : 152) * 4);
+    k_median_init<<<1, 256, 0, s>>>(mst, n);
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        k_median_hist<<<mblocks, 256, 0, s>>>(v, n, mst, shift);
+        k_median_pick<<<1, 64, 0, s>>>(mst, shift, out_dev);
+    }
+    counters().launches += 17;
+    return cudaGetLastError();
+}
+
 cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
     if (t->E_Q >= 0.0 && (!t->has_normals || t->H_Q >= 0.0)) return cudaSuccess;
     if (t->n < 7) {   // fewer than six neighbours: statistic undefined, use 0 (clamped later)
@@ -1256,18 +1272,10 @@ cudaError_t target_nu_stats(TargetDev *t, cudaStream_t s) {
             k_knn6_stats<<<(unsigned)blocks, kKnnBlock, 0, s>>>(ix, sd, sh, flag);
         }
         counters().launches += 1;
-        const unsigned mblocks = (unsigned)std::min<int64_t>((t->n + 255) / 256, (int64_t)(sms > 0 ? sms : 152) * 4);
-        for (int which = 0; which < (sh ? 2 : 1); ++which) {
-            const double *v = which ? sh : sd;
-            k_median_init<<<1, 256, 0, s>>>(mst, (int)t->n);
-            for (int shift = 56; shift >= 0; shift -= 8) {
-                k_median_hist<<<mblocks, 256, 0, s>>>(v, (int)t->n, mst, shift);
-                k_median_pick<<<1, 64, 0, s>>>(mst, shift, out + which);
-            }
-            counters().launches += 17;
-        }
+        for (int which = 0; which < (sh ? 2 : 1); ++which)
+            if (e == cudaSuccess) e = launch_median(which ? sh : sd, (int)t->n, mst, out + which, s);
         double h[3] = {0.0, 0.0, 0.0};
-        e = cudaMemcpyAsync(h, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
         counters().d2h += 3 * sizeof(double);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         int overflow = 0;

@@ -123,6 +123,10 @@ __global__ void __launch_bounds__(128) k_closest(Index ix, const float *__restri
 }
 
 // Single-evaluation set-up for fricp_eval_pass: T is normalised (R, t). One warp.
+__global__ void __launch_bounds__(32) k_after_init(PairState *st, const double *median) {
+    if (threadIdx.x == 0) start_after_init(st, *median);   // nu_max and the first stage, as after a block median
+}
+
 __global__ void __launch_bounds__(32) k_setup_eval(PairState *gst, const double *T) {
     __shared__ double sh[kTeamScratch];
     if (threadIdx.x >= kTeamLanes) return;
@@ -204,6 +208,12 @@ cudaError_t launch_closest(const TargetDev *t, const float *p_dev, int64_t m, co
     }
     cudaFreeAsync(dT, s);
     return e;
+}
+
+cudaError_t launch_after_init(PairState *st, const double *median_dev, cudaStream_t s) {
+    k_after_init<<<1, 32, 0, s>>>(st, median_dev);
+    counters().launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_setup_eval_xi(PairState *st, const double *T_normalized12, cudaStream_t s) {

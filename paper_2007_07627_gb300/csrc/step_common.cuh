@@ -388,7 +388,16 @@ template <int K>
 __device__ __forceinline__ void finish_pass(const StepHead &h, PairState *st, const double *partial, int ntiles,
                                             const double *resid, double *trace, double *sS, double *team_sh) {
     reduce_tiles<K>(partial, ntiles, sS, team_sh);
-    if (h.phase == PH_INIT) {
+    if (h.phase == PH_INIT && st->init_median_ext) {
+        // the host selects the median with the whole GPU (launch_median) and
+        // then starts the first stage (launch_after_init)
+        if (threadIdx.x == 0) {
+            st->device_steps++;
+            if (st->eval_counts) st->corr_passes++;
+            st->counter = 0u;   // the next pass's tile and search tickets start over
+            st->nn_next = 0u;
+        }
+    } else if (h.phase == PH_INIT) {
         const int n = h.M;
         double lo, hi;
         block_median_pair(resid, n, &lo, &hi);
