@@ -335,18 +335,27 @@ struct Best6 {
     float bound;   // d[5] rounded up to float
 };
 
+// Insert (d, o, j) into the six kept in (d, o) order, if it belongs there. Fully
+// unrolled with constant indices, so the six stay in registers: slot s takes
+// the old entry s - 1 while that one orders after the newcomer, the newcomer at
+// the first slot where it does not, and slot 0 if it orders before all.
 __device__ __forceinline__ void best6_insert(Best6 &b, double d, int o, int j) {
     if (!(d < b.d[5] || (d == b.d[5] && o < b.o[5]))) return;
-    int s = 5;
-    while (s > 0 && (b.d[s - 1] > d || (b.d[s - 1] == d && b.o[s - 1] > o))) {
-        b.d[s] = b.d[s - 1];
-        b.o[s] = b.o[s - 1];
-        b.j[s] = b.j[s - 1];
-        --s;
+    bool done = false;
+#pragma unroll
+    for (int s = 5; s >= 1; --s) {
+        const bool after = !done && (b.d[s - 1] > d || (b.d[s - 1] == d && b.o[s - 1] > o));
+        const bool put = !done && !after;
+        b.d[s] = after ? b.d[s - 1] : (put ? d : b.d[s]);
+        b.o[s] = after ? b.o[s - 1] : (put ? o : b.o[s]);
+        b.j[s] = after ? b.j[s - 1] : (put ? j : b.j[s]);
+        done = done || put;
     }
-    b.d[s] = d;
-    b.o[s] = o;
-    b.j[s] = j;
+    if (!done) {
+        b.d[0] = d;
+        b.o[0] = o;
+        b.j[0] = j;
+    }
     b.bound = __double2float_ru(b.d[5]);
 }
 
@@ -573,13 +582,15 @@ __device__ bool tile_knn6(const Index &ix, int g, int i, bool live, const float 
     b.bound = INFINITY;
     const int i0 = 32 * g;
     const float4 mine = live ? __ldg(ix.pts + i) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int t = 0; t < 32; ++t) {   // 1. the tile's own points
+    for (int k = 1; k < 32; ++k) {   // 1. the tile's own points, nearest in Morton order first
+        const int off = (k & 1) ? (k + 1) >> 1 : -(k >> 1);   // +1, -1, +2, -2, ..., -15, +16
+        const int t = (lane + off) & 31;
         float4 q;
         q.x = __shfl_sync(FULL, mine.x, t);
         q.y = __shfl_sync(FULL, mine.y, t);
         q.z = __shfl_sync(FULL, mine.z, t);
         q.w = __shfl_sync(FULL, mine.w, t);
-        if (live && t != lane && i0 + t < ix.n) knn6_offer_own(b, q, xq, i0 + t);
+        if (live && i0 + t < ix.n) knn6_offer_own(b, q, xq, i0 + t);
     }
     float R = live ? b.bound : 0.0f;
 #pragma unroll
@@ -648,11 +659,20 @@ __device__ bool tile_knn6(const Index &ix, int g, int i, bool live, const float 
         sp = base;
         __syncwarp();
     }
-    // 3. every lane offers the candidates' points to its own six
+    // 3. every lane offers the candidates' points to its own six, bucket by
+    //    bucket; a lane whose own bound the bucket's boxes exceed skips it, and
+    //    the warp skips a bucket no lane needs
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
     for (int k = 0; k < nc; ++k) {
-        const int beg = (cand[k] - ix.L) * kLeaf;
-        const int end = min(beg + kLeaf, ix.n);
+        const int c = cand[k];
+        bool need = false;
         if (live)
+            need = box_d2(__ldg(ix.nodes + 2 * c), __ldg(ix.nodes + 2 * c + 1), xq, zero) * kShrink <= b.bound &&
+                   (ix.obb == nullptr || obb_d2(ix.obb + 4 * (c - ix.L), xq, zero) * kObbShrink <= b.bound);
+        if (!__any_sync(FULL, need)) continue;
+        const int beg = (c - ix.L) * kLeaf;
+        const int end = min(beg + kLeaf, ix.n);
+        if (need)
             for (int j = beg; j < end; ++j) knn6_offer_own(b, __ldg(ix.pts + j), xq, j);
     }
     __syncwarp();
