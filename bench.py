@@ -69,7 +69,7 @@ GOLDEN3 = ROOT / "tests" / "golden" / "fullsize_config3_p2pl_welsch.json"
 # search); the solver's algebra (solver.cuh, linalg.cuh) and the median
 # (select.cuh) are compiled into the same file but only the accumulate kernel
 # calls them.
-KNN_SOURCES = ["step.cu", "step_common.cuh", "fricp_internal.cuh"]
+KNN_SOURCES = ["step.cu", "step_common.cuh", "fricp_internal.cuh", "obb.cuh"]
 
 
 def parse():

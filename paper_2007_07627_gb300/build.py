@@ -17,7 +17,8 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libfricp.so"
 SOURCES = ["api.cu", "index.cu", "step.cu", "static_pass.cu", "batch.cu"]
-HEADERS = ["fricp_internal.cuh", "linalg.cuh", "solver.cuh", "select.cuh", "step_common.cuh", "host_common.cuh"]
+HEADERS = ["fricp_internal.cuh", "linalg.cuh", "solver.cuh", "select.cuh", "step_common.cuh", "host_common.cuh",
+           "obb.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

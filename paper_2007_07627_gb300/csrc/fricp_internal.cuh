@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "../../include/fricp.h"
+#include "obb.cuh"
 
 #define FRICP_HD __host__ __device__
 
@@ -246,25 +247,15 @@ __device__ __forceinline__ float box_d2(float4 lo, float4 hi, const float xh[3],
     return fmaf(c, c, fmaf(b, b, a * a));
 }
 
-// Squared distance from x = xh + xl to a bucket's oriented box, in float. The
-// box is built (k_leaf_obb) from the exact float axes it stores, with half-
-// extents widened by 1e-6 relative plus 2e-6 of the bucket's radius; against
-// that widening, the float rounding of u = A ((xh - c) + xl) (at most ~5.2e-7 of
-// |x - c| per axis) leaves the result at most (1 + 8e-6) times the squared
-// distance to the bucket's nearest point. A bucket is skipped only when this
-// distance, shrunk by kObbShrink, still exceeds the bound: it can never hold a
-// point inside the tie window.
+// Squared distance from x = xh + xl to a bucket's oriented box (obb_fit,
+// obb_eval in obb.cuh): at most (1 + 8e-6) times the squared distance to the
+// bucket's nearest point. A bucket is skipped only when this distance, shrunk by
+// kObbShrink, still exceeds the bound: it can never hold a point inside the tie
+// window.
 constexpr float kObbShrink = 1.0f - 2e-5f;
 
 __device__ __forceinline__ float obb_d2(const float4 *o, const float xh[3], const float xl[3]) {
-    const float4 c = __ldg(o), a0 = __ldg(o + 1), a1 = __ldg(o + 2), a2 = __ldg(o + 3);
-    const float dx = (xh[0] - c.x) + xl[0];
-    const float dy = (xh[1] - c.y) + xl[1];
-    const float dz = (xh[2] - c.z) + xl[2];
-    const float e0 = fmaxf(fabsf(fmaf(a0.z, dz, fmaf(a0.y, dy, a0.x * dx))) - c.w, 0.0f);
-    const float e1 = fmaxf(fabsf(fmaf(a1.z, dz, fmaf(a1.y, dy, a1.x * dx))) - a0.w, 0.0f);
-    const float e2 = fmaxf(fabsf(fmaf(a2.z, dz, fmaf(a2.y, dy, a2.x * dx))) - a1.w, 0.0f);
-    return fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
+    return obb_eval(__ldg(o), __ldg(o + 1), __ldg(o + 2), __ldg(o + 3), xh, xl);
 }
 
 // Box test of a search lane: xdn <= x <= xup on every axis, so lo - xup and
