@@ -18,8 +18,12 @@ widened to float64:
   * Anderson acceleration (Sec. 4.1, Eq. 6) with numpy's Householder QR;
   * Algorithm 1 (Welsch point-to-point, and with psi -> squared distance,
     w == 1 and a single stage, the accelerated point-to-point "Fast ICP");
-  * Algorithm 2 (Welsch point-to-plane) with the App. D gradient;
-  * the nu_max / nu_min rules (Sec. 4.3, Sec. 5, App. C).
+  * Algorithm 2 (Welsch point-to-plane) with the App. D gradient, and the
+    plain point-to-plane objective of Eq. (15) under it;
+  * the Welsch-robust symmetric objective Sec. 7 proposes as future work, read
+    as Algorithm 2 on the residual of symmetric_residual;
+  * the nu_max / nu_min rules (Sec. 4.3, Sec. 5, App. C);
+  * normals from the k nearest neighbours (Sec. 6, estimate_normals).
 Where the paper is silent, garbled or inconsistent the reading taken is a named
 constant or a commented branch below, each citing the passage it reads.
 
