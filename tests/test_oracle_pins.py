@@ -694,7 +694,11 @@ def test_registration_with_kdtree_correspondences_equals_bruteforce():
         for key in ("iterations", "corr_passes", "reverts", "line_search_trials", "stages"):
             assert a[key] == b[key]
         assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["t"], b["t"])
-        assert np.array_equal(a["trace"], b["trace"])
+        # every counter, R and t agree bit for bit; an energy has been seen to differ
+        # by one ulp between the two runs in about one process in twenty (a library
+        # reduction whose order is not fixed from one process to the next), so the
+        # energies are compared to rounding
+        assert np.allclose(a["trace"], b["trace"], rtol=1e-14, atol=0.0)
 
 
 # --------------------------------------------------------------------------
