@@ -253,8 +253,9 @@ fricp_status fricp_register_recorded(const fricp_target *target, const float *p_
  * target needs normals. p_normals: float32 [m][3] in p_xyz's memory space,
  * each a unit normal (within 1e-3) or zero for a point without a normal, whose
  * residual is then the point-to-plane one (with every np_i zero the
- * registration is FRICP_P2PL_WELSCH_AA's, bit for bit). Other arguments as fricp_register_recorded (steps may be NULL with
- * steps_capacity 0). The batched and served engines do not run this variant.
+ * registration is FRICP_P2PL_WELSCH_AA's, bit for bit). Other arguments as
+ * fricp_register_recorded (steps may be NULL with steps_capacity 0). The
+ * batched and served engines do not run this variant.
  * Errors: as fricp_register; EINVAL for a source normal neither zero nor unit. */
 fricp_status fricp_register_symmetric(const fricp_target *target, const float *p_xyz, const float *p_normals,
                                       int64_t m, int32_t on_device, const double *T0,
